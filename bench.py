@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Benchmark of the Axilrod-Teller three-body engine on one GB300.
+
+Headline step: one exhaustive FP32-bulk solve of Phi for the N = 32 768
+uniform workload (cube of side 32, minimum pair distance 0.5, seed 2), i.e.
+all C(N,3) = 5.8635e12 unordered triples. The metric is triples/s.
+
+The JSON line also carries, for context: the FP64 exhaustive rate,
+the multi-tree particles/s at eps = 1e-2 on the 2^20-point Gaussian mixture
+(when built), the roofline of the dominant kernel, the CPU oracle baseline,
+an end-to-end number through the host-buffer C entry point, and the SM
+clocks sampled during the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (the exhaustive sum
+needs no exchange for one system); value = all ranks' triples / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AT triples/s (exhaustive) & particles/s at eps=1e-2 vs plain FP64; p50/p99 ms"
+WORKLOAD = "exh32_n32768"
+N_MAIN = 32768
+FLOPS_PER_TRIPLE_FP32 = 25   # counted from the inner loop (FMA = 2), see csrc/tile_fp32.cuh
+FP32_LANES_PER_SM = 128
+
+
+def triples(n):
+    return n * (n - 1) * (n - 2) // 6
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling every 200 ms during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(X, n_particles, seed=2024):
+    """Oracle Phi for a bounded seeded sample of particles on all host cores;
+    returns (triples/s of the whole job, seconds, particles, threads)."""
+    import oracle
+    from paper_1105_2769_gb300 import inputs
+    oracle.build()
+    nt = oracle.max_threads()
+    m = n_particles or nt
+    idx = inputs.sample_indices(len(X), m, seed)
+    t0 = time.perf_counter()
+    oracle.phi(X, idx, nthreads=nt)
+    dt = time.perf_counter() - t0
+    n = len(X)
+    evals = m * (n - 1) * (n - 2) / 2          # phi evaluations done
+    return evals / 3.0 / dt, dt, m, nt        # full job = 3 C(N,3) evaluations
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1105_2769_gb300 import inputs
+    X = inputs.workload(WORKLOAD)
+    import oracle
+    oracle.build()
+    nt = oracle.max_threads()
+    rates = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_oracle_rate(X, nt)
+    total_t = 0.0
+    for _ in range(args.steps):
+        r, dt, m, nt = cpu_oracle_rate(X, nt)
+        rates.append(r)
+        total_t += dt
+    value = sum(rates) / len(rates)
+    sample = (f"{nt} seeded particles per step of the N={N_MAIN} set (each a full "
+              f"C(N-1,2) sum); job-equivalent triples = evaluations/3")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "triples/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_MAIN, "distribution": "uniform [0,32]^3, d_min 0.5, seed 2"},
+        "cpu_baseline": {"value": value, "unit": "triples/s", "cores": nt, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "triples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64/tree/serving context")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1105_2769_gb300 import api, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    X = inputs.workload(WORKLOAD)
+    Xd = torch.from_numpy(X).to(dev)
+    ctx = api.default_context(local)
+    ctx.set_timing(True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    phi = torch.empty(len(X), dtype=torch.float64, device=dev)
+
+    for _ in range(args.warmup):
+        api.potential(Xd, mode="fp32", out=phi)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    for s in range(args.steps):
+        flush.zero_()                      # evict L2 between steps
+        starts[s].record(stream)
+        api.potential(Xd, mode="fp32", out=phi)
+        ends[s].record(stream)
+        kernel_ms.append(ctx.last_kernel_ms())
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    n_trip = triples(len(X))
+    value = world * n_trip * args.steps / (tot_ms / 1e3)
+
+    # roofline of the dominant kernel (FP32 ALU bound)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    k_ms = sum(kernel_ms) / len(kernel_ms)
+    achieved = FLOPS_PER_TRIPLE_FP32 * n_trip / (k_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None,
+                "peak_note": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "flops_per_triple": FLOPS_PER_TRIPLE_FP32, "kernel_ms": k_ms}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (peak_tflops * clocks["sm_mhz"] / sm_max)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    Xh = torch.from_numpy(X).pin_memory().numpy()
+    ph = torch.empty(len(X), dtype=torch.float64).pin_memory().numpy()
+    api.potential_host(Xh, mode="fp32", out=ph)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        api.potential_host(Xh, mode="fp32", out=ph)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world * n_trip / e2e_s, "unit": "triples/s",
+           "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(ph.nbytes)}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        # plain FP64 exhaustive rate on the same distribution (density 1, d_min 0.5)
+        n64 = 8192
+        X64 = inputs.uniform_cube(n64, 32.0 * (n64 / N_MAIN) ** (1 / 3), 0.5, 2)
+        X64d = torch.from_numpy(X64).to(dev)
+        api.potential(X64d, mode="fp64")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        api.potential(X64d, mode="fp64")
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        r64 = triples(n64) / dt
+        extras["fp64_exhaustive"] = {"n": n64, "triples_per_s": r64,
+                                     "fp32_over_fp64": value / world / r64}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "triples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": len(X), "triples_per_step": n_trip,
+                   "distribution": "uniform [0,32]^3, d_min 0.5, seed 2",
+                   "precision": "FP32 triple arithmetic, FP64 accumulation",
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+    }
+    line.update(extras)
+    if rank == 0 and not args.no_cpu_baseline:
+        r, dt, m, nt = cpu_oracle_rate(X, 0)
+        line["cpu_baseline"] = {"value": r, "unit": "triples/s", "cores": nt, "kind": "oracle",
+                                "sample": f"{m} seeded particles of the N={len(X)} set, "
+                                          f"{dt:.1f} s; job-equivalent triples = evaluations/3"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

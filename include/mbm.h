@@ -1,0 +1,171 @@
+/*
+ * mbm.h - C ABI of the GB300 Axilrod-Teller three-body engine.
+ *
+ * The library computes, for every particle x_i of a 3-D point set X,
+ *
+ *   Phi(x_i) = sum_{j<k; j,k != i} phi(x_i, x_j, x_k)                (Eq. 1, n = 3)
+ *   phi(x_i,x_j,x_k) = (1 + 3 cos t_i cos t_j cos t_k)
+ *                      / (r_ij^3 r_ik^3 r_jk^3)                       (Sec. 1, Axilrod-Teller)
+ *
+ * exactly (every unordered triple once, credited to its three members), or
+ * approximately by the multi-tree method of Lee, Ozakin & Gray (Algorithm 2
+ * with the p = 0 bounds of Sec. 4 and the Monte Carlo rules of
+ * Algorithms 3-5), under the error criteria of Definitions 2.1-2.3.
+ *
+ * Conventions shared by every entry point:
+ *   - X is N x 3 row-major FP64 (x0 y0 z0 x1 y1 z1 ...), caller-owned.
+ *   - Outputs are caller-owned FP64 arrays. "_dev" pointers are device
+ *     memory of the context's GPU; "_host" pointers are host memory.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and is asynchronous unless the entry point says otherwise.
+ *     The caller must keep inputs and outputs alive until the stream has
+ *     passed the call.
+ *   - N < 3: the sum is empty, outputs are zeroed, MBM_OK (Eq. 1).
+ *   - No exception crosses the ABI; every entry point returns a status and
+ *     mbm_last_error() gives a thread-local message for the last failure.
+ *   - The library owns its scratch memory (packed coordinates, work
+ *     counters, trees); it is charged against the context's HBM budget.
+ */
+#ifndef MBM_H
+#define MBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* mbm_stream_t; /* same handle as cudaStream_t */
+
+typedef enum {
+    MBM_OK = 0,
+    MBM_PENDING = 1,     /* mbm_poll: request not finished yet */
+    MBM_EINVAL = -1,     /* bad argument, non-finite or coincident points */
+    MBM_ENOMEM = -2,     /* device allocation failed */
+    MBM_EBUDGET = -3,    /* request does not fit the context's HBM budget */
+    MBM_EOVERFLOW = -4,  /* a bounded device work list overflowed */
+    MBM_ETIMEDOUT = -5,  /* a bounded wait ran out */
+    MBM_ECUDA = -6,      /* a CUDA runtime call failed */
+    MBM_ENOTSUP = -7     /* mode not supported by this entry point */
+} mbm_status;
+
+/* Modes of mbm_potential / mbm_forces. */
+enum {
+    MBM_EXH_FP64 = 0, /* exhaustive, FP64 everywhere */
+    MBM_EXH_FP32 = 1, /* exhaustive, FP32 triple arithmetic, FP64 accumulation */
+    MBM_TREE = 2,     /* multi-tree approximation (Algorithm 2) */
+    MBM_ABS = 0x100   /* with MBM_TREE: eps is the absolute bound tau (Def. 2.1) */
+};
+
+/* Tuning and semantics of the tree path (Sec. 3-4). */
+typedef struct {
+    double tau;        /* absolute error term of Def. 2.3 (0 = pure relative) */
+    int32_t leaf_size; /* leaf threshold of Algorithm 1 (default 32, max 32) */
+    int32_t m_limit;   /* Monte Carlo sample cap of Algorithm 4 (default 256) */
+    double zeta;       /* speed-up factor of Algorithm 3 (default 4) */
+    uint64_t seed;     /* Philox key for Monte Carlo draws */
+    int32_t mc_rule;   /* 0 = relative stop test with T_i on both terms, 1 = as printed */
+    int32_t validate;  /* 1: synchronise and report non-finite/coincident input */
+    int32_t reserved[6];
+} mbm_config;
+
+/* Counters of the last solve (tree path); all zero for exhaustive modes. */
+typedef struct {
+    int64_t node_triples_visited;
+    int64_t det_prunes;
+    int64_t mc_prunes;
+    int64_t mc_attempts;
+    int64_t base_cases;
+    int64_t base_triples;   /* point triples evaluated exactly */
+    int64_t mc_samples;     /* phi evaluations drawn by Monte Carlo */
+    int64_t levels;         /* traversal levels */
+    double ms_build, ms_seed, ms_traverse, ms_base, ms_finalize;
+} mbm_stats;
+
+typedef struct mbm_ctx mbm_ctx;
+typedef struct mbm_tree mbm_tree;
+
+/* Version string of the library. */
+const char* mbm_version(void);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* mbm_last_error(void);
+
+/* Fill *cfg with the defaults listed above. */
+void mbm_config_default(mbm_config* cfg);
+
+/* Create a context on CUDA device `device` whose library-owned device
+ * memory may not exceed `hbm_budget_bytes` (0 = no limit). *out is
+ * owned by the caller and released with mbm_ctx_destroy. */
+mbm_status mbm_ctx_create(int device, size_t hbm_budget_bytes, mbm_ctx** out);
+
+/* Synchronise the device and free every library-owned buffer. */
+mbm_status mbm_ctx_destroy(mbm_ctx* ctx);
+
+/* Library-owned device bytes currently held by the context. */
+size_t mbm_ctx_bytes_in_use(const mbm_ctx* ctx);
+
+/* Enable (1) or disable (0) CUDA-event timing of each solve's dominant
+ * kernel (the exhaustive kernel, or the tree path's base-case kernels).
+ * Events are recorded on the solve's stream. */
+mbm_status mbm_ctx_set_timing(mbm_ctx* ctx, int enable);
+
+/* Milliseconds spent in the dominant kernel(s) of the last timed solve;
+ * waits for that solve's end event. Returns -1 if nothing was timed. */
+double mbm_ctx_last_kernel_ms(mbm_ctx* ctx);
+
+/*
+ * Phi(x_i) for all i (Eq. 1 with the Axilrod-Teller phi of Sec. 1).
+ *   X_dev   : N x 3 FP64 device array, read only.
+ *   phi_dev : N FP64 device array, written (fully overwritten).
+ *   mode    : MBM_EXH_FP64, MBM_EXH_FP32, or MBM_TREE[|MBM_ABS].
+ *   eps     : tree modes only; relative bound of Def. 2.2 (or tau with
+ *             MBM_ABS, Def. 2.1). Must be >= 0.
+ *   alpha   : tree modes only; failure probability of Def. 2.3, in [0, 1).
+ *             alpha = 0 selects the deterministic rule.
+ * Errors: MBM_EINVAL for N < 0, NULL pointers, eps < 0, alpha outside
+ * [0, 1), an unknown mode; with cfg->validate (default on in
+ * mbm_potential) also for non-finite coordinates or two coincident points,
+ * detected on the device and reported after a stream synchronisation.
+ */
+mbm_status mbm_potential(mbm_ctx* ctx, const double* X_dev, int64_t N, double eps,
+                         double alpha, int mode, double* phi_dev, mbm_stream_t stream);
+
+/* As mbm_potential, with explicit configuration (NULL = defaults), an
+ * optional prebuilt tree for MBM_TREE (NULL = build one internally) and an
+ * optional stats record (NULL = not reported; filling it synchronises). */
+mbm_status mbm_potential_ex(mbm_ctx* ctx, const double* X_dev, int64_t N, double eps,
+                            double alpha, int mode, const mbm_config* cfg, mbm_tree* tree,
+                            double* phi_dev, mbm_stats* stats, mbm_stream_t stream);
+
+/* Host-buffer variant: copies X_host to the device, runs mbm_potential_ex
+ * and copies Phi back to phi_host, then synchronises `stream`.
+ * Device buffers are library-owned scratch. */
+mbm_status mbm_potential_host(mbm_ctx* ctx, const double* X_host, int64_t N, double eps,
+                              double alpha, int mode, const mbm_config* cfg,
+                              double* phi_host, mbm_stream_t stream);
+
+/*
+ * Forces F_i = -dE/dx_i of the total energy E = sum_{a<b<c} phi_abc
+ * (no counterpart in the paper; the derivative of Eq. 1's summand).
+ *   F_dev : N x 3 FP64 device array, written.
+ *   mode  : MBM_EXH_FP64 or MBM_EXH_FP32 (tree forces: MBM_ENOTSUP).
+ */
+mbm_status mbm_forces(mbm_ctx* ctx, const double* X_dev, int64_t N, double eps, double alpha,
+                      int mode, double* F_dev, mbm_stream_t stream);
+
+/*
+ * Vector-Jacobian product of Phi: gradX_m = d/dx_m sum_l g_l Phi(x_l)
+ * = sum over triples t containing m of (g_a + g_b + g_c) d phi_t/d x_m.
+ *   g_dev     : N FP64 device array (cotangent of Phi).
+ *   gradX_dev : N x 3 FP64 device array, written.
+ *   mode      : MBM_EXH_FP64 or MBM_EXH_FP32.
+ */
+mbm_status mbm_potential_vjp(mbm_ctx* ctx, const double* X_dev, int64_t N, const double* g_dev,
+                             int mode, double* gradX_dev, mbm_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MBM_H */

@@ -1,0 +1,87 @@
+"""ctypes bindings of the tree-path oracle (tree_oracle.c). Test infrastructure only."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+_L = None
+
+
+def bind(L):
+    global _L
+    i64, dbl, vp = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    L.oracle_tree_potential.argtypes = [vp, i64, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int, dbl,
+                                        ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+    L.oracle_tree_layout.argtypes = [vp, i64, ctypes.c_int, vp, vp, vp, vp, vp, vp]
+    L.oracle_tree_depth.argtypes = [i64, ctypes.c_int]
+    L.oracle_philox4x32_10.argtypes = [vp, vp, vp]
+    L.oracle_z_two_sided.argtypes = [dbl]
+    L.oracle_z_two_sided.restype = dbl
+    L.oracle_phi_interval.argtypes = [vp, vp, vp, vp]
+    _L = L
+
+
+def _lib():
+    if _L is None:
+        import oracle
+        oracle.lib()
+    return _L
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def tree_potential(X, eps=0.0, tau=0.0, alpha=0.0, leaf_size=32, m_limit=256, zeta=4.0,
+                   seed=0x5eed5eed, mc_rule=0, seed_up=2, with_counts=False):
+    """Serial restatement of the multi-tree algorithm; returns (Phi, counts, stats)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n = len(X)
+    out = np.zeros(n)
+    counts = np.zeros(n, dtype=np.int64) if with_counts else None
+    stats = np.zeros(6, dtype=np.int64)
+    rc = _lib().oracle_tree_potential(_p(X), n, float(eps), float(tau), float(alpha),
+                                      int(leaf_size), int(m_limit), float(zeta), int(seed),
+                                      int(mc_rule), int(seed_up), _p(out),
+                                      _p(counts) if with_counts else None, _p(stats))
+    if rc != 0:
+        raise RuntimeError("oracle_tree_potential failed")
+    keys = ["visited", "det_prunes", "mc_prunes", "mc_attempts", "base_cases", "mc_samples"]
+    return out, counts, dict(zip(keys, stats.tolist()))
+
+
+def tree_layout(X, leaf_size=32):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n = len(X)
+    depth = _lib().oracle_tree_depth(n, leaf_size)
+    m = (2 << depth) - 1
+    perm = np.zeros(n, dtype=np.int64)
+    begin = np.zeros(m, dtype=np.int64)
+    end = np.zeros(m, dtype=np.int64)
+    lo = np.zeros((m, 3)); hi = np.zeros((m, 3)); cen = np.zeros((m, 3))
+    _lib().oracle_tree_layout(_p(X), n, int(leaf_size), _p(perm), _p(begin), _p(end), _p(lo),
+                              _p(hi), _p(cen))
+    return {"depth": depth, "perm": perm, "begin": begin, "end": end, "lo": lo, "hi": hi,
+            "cen": cen}
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _lib().oracle_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def z_two_sided(alpha):
+    return float(_lib().oracle_z_two_sided(float(alpha)))
+
+
+def phi_interval(sq_lo, sq_hi):
+    """[phi_lo, phi_hi] for squared side intervals (c: slots 1-2, b: 1-3, a: 2-3)."""
+    lo = np.ascontiguousarray(sq_lo, dtype=np.float64)
+    hi = np.ascontiguousarray(sq_hi, dtype=np.float64)
+    a = np.zeros(1); b = np.zeros(1)
+    _lib().oracle_phi_interval(_p(lo), _p(hi), _p(a), _p(b))
+    return float(a[0]), float(b[0])

@@ -1,0 +1,174 @@
+"""Python API over the C ABI (torch device memory and streams).
+
+    potential(X, eps=0.0, alpha=0.0, mode="fp32")   -> Phi, shape (N,), float64
+    forces(X, mode="fp32")                          -> F, shape (N, 3)
+    potential_vjp(X, g, mode="fp32")                -> d(g . Phi)/dX
+    Potential.apply(X)                              -> Phi with autograd
+
+``X`` is a CUDA float64 tensor of shape (N, 3). Modes: "fp64" (exhaustive,
+FP64 everywhere), "fp32" (exhaustive, FP32 triple arithmetic with FP64
+accumulation), "tree" (multi-tree approximation with relative ``eps``),
+"tree_abs" (multi-tree with absolute bound ``eps`` = tau). All work runs on
+the current torch CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+import torch
+
+from . import _lib
+
+MODES = {"fp64": _lib.MBM_EXH_FP64, "fp32": _lib.MBM_EXH_FP32, "tree": _lib.MBM_TREE,
+         "tree_abs": _lib.MBM_TREE | _lib.MBM_ABS}
+
+_ctx_lock = threading.Lock()
+_contexts = {}
+
+
+class Context:
+    """Owns an ``mbm_ctx`` (scratch arena, status word) on one device."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        L = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(L.mbm_ctx_create(int(device), int(hbm_budget_bytes), ctypes.byref(h)))
+        self.handle = h
+        self.device = device
+
+    def set_timing(self, enable: bool = True):
+        """Record CUDA events around each solve's dominant kernel."""
+        _lib.check(_lib.load().mbm_ctx_set_timing(self.handle, int(bool(enable))))
+
+    def last_kernel_ms(self) -> float:
+        """Dominant-kernel time of the last timed solve (waits for it)."""
+        return float(_lib.load().mbm_ctx_last_kernel_ms(self.handle))
+
+    def bytes_in_use(self) -> int:
+        return int(_lib.load().mbm_ctx_bytes_in_use(self.handle))
+
+    def close(self):
+        if self.handle:
+            _lib.load().mbm_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown order varies
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_context(device=None) -> Context:
+    if device is None:
+        device = torch.cuda.current_device()
+    with _ctx_lock:
+        ctx = _contexts.get(device)
+        if ctx is None:
+            ctx = Context(device)
+            _contexts[device] = ctx
+    return ctx
+
+
+def _mode(mode) -> int:
+    if isinstance(mode, int):
+        return mode
+    try:
+        return MODES[mode]
+    except KeyError:
+        raise ValueError(f"unknown mode {mode!r}; expected one of {sorted(MODES)}") from None
+
+
+def _check_points(X: torch.Tensor) -> torch.Tensor:
+    if not isinstance(X, torch.Tensor) or not X.is_cuda:
+        raise TypeError("X must be a CUDA tensor")
+    if X.dim() != 2 or X.shape[1] != 3:
+        raise ValueError("X must have shape (N, 3)")
+    if X.dtype != torch.float64:
+        X = X.to(torch.float64)
+    return X.contiguous()
+
+
+def _stream_handle() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def potential(X: torch.Tensor, eps: float = 0.0, alpha: float = 0.0, mode="fp32",
+              config: _lib.Config | None = None, tree=None, stats: bool = False,
+              ctx: Context | None = None, out: torch.Tensor | None = None):
+    """Phi(x_i) for every particle (Eq. 1 with the Axilrod-Teller phi)."""
+    X = _check_points(X)
+    n = X.shape[0]
+    ctx = ctx or default_context(X.device.index)
+    phi = out if out is not None else torch.empty(n, dtype=torch.float64, device=X.device)
+    cfg = config if config is not None else _lib.default_config()
+    st = _lib.Stats()
+    L = _lib.load()
+    _lib.check(L.mbm_potential_ex(ctx.handle, ctypes.c_void_p(X.data_ptr()), n, float(eps),
+                                  float(alpha), _mode(mode), ctypes.byref(cfg),
+                                  tree.handle if tree is not None else None,
+                                  ctypes.c_void_p(phi.data_ptr()),
+                                  ctypes.byref(st) if stats else None, _stream_handle()))
+    return (phi, st.as_dict()) if stats else phi
+
+
+def potential_host(X: np.ndarray, eps: float = 0.0, alpha: float = 0.0, mode="fp32",
+                   config: _lib.Config | None = None, ctx: Context | None = None,
+                   out: np.ndarray | None = None) -> np.ndarray:
+    """Host-buffer entry point: X and the result live in host memory."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    if X.ndim != 2 or X.shape[1] != 3:
+        raise ValueError("X must have shape (N, 3)")
+    n = X.shape[0]
+    ctx = ctx or default_context()
+    phi = out if out is not None else np.empty(n, dtype=np.float64)
+    cfg = config if config is not None else _lib.default_config()
+    _lib.check(_lib.load().mbm_potential_host(
+        ctx.handle, X.ctypes.data_as(ctypes.c_void_p), n, float(eps), float(alpha), _mode(mode),
+        ctypes.byref(cfg), phi.ctypes.data_as(ctypes.c_void_p), _stream_handle()))
+    return phi
+
+
+def forces(X: torch.Tensor, mode="fp32", eps: float = 0.0, alpha: float = 0.0,
+           ctx: Context | None = None) -> torch.Tensor:
+    """F_i = -dE/dx_i, E = sum over unordered triples of phi."""
+    X = _check_points(X)
+    ctx = ctx or default_context(X.device.index)
+    F = torch.empty_like(X)
+    _lib.check(_lib.load().mbm_forces(ctx.handle, ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                      float(eps), float(alpha), _mode(mode),
+                                      ctypes.c_void_p(F.data_ptr()), _stream_handle()))
+    return F
+
+
+def potential_vjp(X: torch.Tensor, g: torch.Tensor, mode="fp32",
+                  ctx: Context | None = None) -> torch.Tensor:
+    """d/dX of sum_l g_l Phi_l."""
+    X = _check_points(X)
+    g = g.detach().to(device=X.device, dtype=torch.float64).contiguous()
+    if g.shape != (X.shape[0],):
+        raise ValueError("g must have shape (N,)")
+    ctx = ctx or default_context(X.device.index)
+    G = torch.empty_like(X)
+    _lib.check(_lib.load().mbm_potential_vjp(ctx.handle, ctypes.c_void_p(X.data_ptr()),
+                                             X.shape[0], ctypes.c_void_p(g.data_ptr()),
+                                             _mode(mode), ctypes.c_void_p(G.data_ptr()),
+                                             _stream_handle()))
+    return G
+
+
+class Potential(torch.autograd.Function):
+    """Phi(X) with a backward pass through the adjoint kernel."""
+
+    @staticmethod
+    def forward(ctx, X, mode="fp32"):
+        ctx.save_for_backward(X)
+        ctx.mode = mode
+        return potential(X.detach(), mode=mode)
+
+    @staticmethod
+    def backward(ctx, grad_phi):
+        (X,) = ctx.saved_tensors
+        return potential_vjp(X.detach(), grad_phi, mode=ctx.mode).to(X.dtype), None

@@ -1,0 +1,333 @@
+// Exhaustive Axilrod-Teller sums on the GPU (every unordered triple once).
+//
+// Phi(x_i) = sum_{j<k; j,k != i} phi(x_i, x_j, x_k)   (Eq. 1, n = 3; Sec. 1)
+//
+// Each unordered triple a < b < c is evaluated once and credited to all
+// three members, which is the same sum (each triple appears in exactly the
+// three slices Phi(x_a), Phi(x_b), Phi(x_c)).
+//
+// FP32 bulk evaluates each triple in the direction-cosine form (see
+// tile_fp32.cuh: unit edge vectors and r^-3 per pair, 16 FP32 operations and
+// 25 FLOPs per triple). FP64 evaluates the law-of-cosines form on squared
+// side lengths c = r_ij^2, b = r_ik^2, a = r_jk^2:
+//   cos t_i cos t_j cos t_k = P / (8abc),  P = (b+c-a)(a+c-b)(a+b-c),
+//   phi = (abc + 0.375 P) A B C,  A = a^(-5/2), B = b^(-5/2), C = c^(-5/2).
+//
+// Work decomposition (both precisions): particles are cut into tiles of 32.
+// A CTA owns one tile pair (J, K), J <= K, and its warps sweep every tile
+// I <= J; a lane owns one particle i of I. Pair quantities are hoisted to
+// the loop level where they are constant: (j,k) in a shared-memory table
+// built once per CTA item, (i,k) once per I tile, (i,j) once per j.
+// Diagonal tiles (I = J, J = K) are handled by zeroing the pair factor of
+// out-of-order pairs, so masked triples contribute exactly 0. Items come
+// from a global counter, largest (most I tiles) first.
+#include "device_math.cuh"
+#include "mbm_internal.h"
+#include "tile_fp32.cuh"
+
+namespace {
+
+constexpr int kTile = 32;
+constexpr int kWarps32 = 8;   // FP32 kernel: 8 warps per CTA
+constexpr int kWarps64 = 4;   // FP64 kernel: 4 warps per CTA
+
+// ---------------------------------------------------------------------------
+// Step a1: input pack.
+// ---------------------------------------------------------------------------
+__global__ void pack_hilo_kernel(const double* __restrict__ X, int64_t N, float4* __restrict__ xh,
+                                 float4* __restrict__ xl, int* __restrict__ flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(flags, MBM_FLAG_NONFINITE);
+        const float hx = (float)x, hy = (float)y, hz = (float)z;
+        xh[i] = make_float4(hx, hy, hz, 0.f);
+        xl[i] = make_float4((float)(x - (double)hx), (float)(y - (double)hy),
+                            (float)(z - (double)hz), 0.f);
+    }
+}
+
+__global__ void pack_f64_kernel(const double* __restrict__ X, int64_t N, double4* __restrict__ x4,
+                                int* __restrict__ flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(flags, MBM_FLAG_NONFINITE);
+        x4[i] = make_double4(x, y, z, 0.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step a3, FP32 bulk: FP32 triple arithmetic (direction-cosine form, see
+// tile_fp32.cuh), per-tile FP32 partial sums, FP64 accumulation across tiles.
+// ---------------------------------------------------------------------------
+struct Fp32Smem {
+    mbm_tile::TabPair tab[kTile][kTile / 2];
+    float4 sJh[kTile], sJl[kTile], sKh[kTile], sKl[kTile];
+    float redJ[kWarps32][kTile][kTile + 1];
+    float redK[kWarps32][kTile][kTile + 1];
+    double wsum[2][kWarps32][kTile];
+    long long item;
+};
+
+__global__ void __launch_bounds__(kWarps32 * 32, 2)
+exh_fp32_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int N, int NT,
+                long long n_items, unsigned long long* __restrict__ counter,
+                double* __restrict__ phi, int* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Fp32Smem& sm = *reinterpret_cast<Fp32Smem*>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    for (;;) {
+        if (threadIdx.x == 0) sm.item = (long long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const long long t = sm.item;
+        if (t >= n_items) break;
+        int J, K;
+        decode_pair_item(t, NT, J, K);
+        const int nJ = min(kTile, N - J * kTile), nK = min(kTile, N - K * kTile);
+        if (threadIdx.x < kTile) {
+            const int j = J * kTile + threadIdx.x;
+            sm.sJh[threadIdx.x] = j < N ? xh[j] : zero4;
+            sm.sJl[threadIdx.x] = j < N ? xl[j] : zero4;
+        } else if (threadIdx.x < 2 * kTile) {
+            const int kk = threadIdx.x - kTile, k = K * kTile + kk;
+            sm.sKh[kk] = k < N ? xh[k] : zero4;
+            sm.sKl[kk] = k < N ? xl[k] : zero4;
+        }
+        __syncthreads();
+        // (j,k) table; every unordered pair of the set is a valid entry of
+        // exactly one table, which is where coincident points are caught.
+        bool bad = false;
+        for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+            const int jj = e >> 5, kk = e & 31;
+            const bool v = jj < nJ && kk < nK && (J != K || jj < kk);
+            bad |= mbm_tile::build_table_entry(sm.tab, jj, kk, sm.sJh[jj], sm.sJl[jj], sm.sKh[kk],
+                                               sm.sKl[kk], v);
+        }
+        if (bad) atomicOr(flags, MBM_FLAG_COINCIDENT);
+        __syncthreads();
+
+        double run_j = 0.0, run_k = 0.0;
+        for (int I = warp; I <= J; I += kWarps32) {
+            const int i = I * kTile + lane;
+            const bool iv = i < N;
+            const float4 ih = iv ? xh[i] : zero4;
+            const float4 il = iv ? xl[i] : zero4;
+            const float acc_i = mbm_tile::tile_triples(sm.tab, sm.sJh, sm.sJl, sm.sKh, sm.sKl, ih,
+                                                       il, iv, lane, nJ, nK, I == J, I == K,
+                                                       sm.redJ[warp], sm.redK[warp]);
+            run_j += (double)mbm_tile::row_sum(sm.redJ[warp], lane);
+            run_k += (double)mbm_tile::row_sum(sm.redK[warp], lane);
+            __syncwarp();
+            if (iv) atomicAdd(&phi[i], (double)acc_i);
+        }
+        sm.wsum[0][warp][lane] = run_j;
+        sm.wsum[1][warp][lane] = run_k;
+        __syncthreads();
+        if (warp < 2) {
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarps32; ++w) tot += sm.wsum[warp][w][lane];
+            const int idx = (warp == 0 ? J : K) * kTile + lane;
+            if (idx < N) atomicAdd(&phi[idx], tot);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step a2 in FP64: the same decomposition with FP64 everywhere. Per-lane
+// (i,k) quantities live in per-warp shared memory (FP64 registers would not
+// fit), the (j,k) table in shared memory, accumulators in registers.
+// ---------------------------------------------------------------------------
+struct Fp64Smem {
+    double2 tab[kTile][kTile];             // (a, A) for (j, k)
+    double2 bw[kWarps64][kTile][kTile];    // (b, B) for (k, lane)
+    double red[kWarps64][kTile][kTile + 1];
+    double wsum[2][kWarps64][kTile];
+    double4 sJ[kTile], sK[kTile];
+    long long item;
+};
+
+__global__ void __launch_bounds__(kWarps64 * 32, 1)
+exh_fp64_kernel(const double4* __restrict__ x4, int N, int NT, long long n_items,
+                unsigned long long* __restrict__ counter, double* __restrict__ phi,
+                int* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Fp64Smem& sm = *reinterpret_cast<Fp64Smem*>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const double4 zero4 = make_double4(0.0, 0.0, 0.0, 0.0);
+
+    for (;;) {
+        if (threadIdx.x == 0) sm.item = (long long)atomicAdd(counter, 1ULL);
+        __syncthreads();
+        const long long t = sm.item;
+        if (t >= n_items) break;
+        int J, K;
+        decode_pair_item(t, NT, J, K);
+        if (threadIdx.x < kTile) {
+            const int j = J * kTile + threadIdx.x;
+            sm.sJ[threadIdx.x] = j < N ? x4[j] : zero4;
+        } else if (threadIdx.x < 2 * kTile) {
+            const int kk = threadIdx.x - kTile, k = K * kTile + kk;
+            sm.sK[kk] = k < N ? x4[k] : zero4;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+            const int jj = e >> 5, kk = e & 31;
+            const int j = J * kTile + jj, k = K * kTile + kk;
+            double a = 1.0, A = 0.0;
+            if (j < N && k < N && (J != K || jj < kk)) {
+                const double dx = sm.sJ[jj].x - sm.sK[kk].x;
+                const double dy = sm.sJ[jj].y - sm.sK[kk].y;
+                const double dz = sm.sJ[jj].z - sm.sK[kk].z;
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 > 0.0) {
+                    a = d2;
+                    A = inv_pow52d(d2);
+                } else {
+                    atomicOr(flags, MBM_FLAG_COINCIDENT);
+                }
+            }
+            sm.tab[jj][kk] = make_double2(a, A);
+        }
+        __syncthreads();
+
+        double run_j = 0.0, run_k = 0.0;
+        for (int I = warp; I <= J; I += kWarps64) {
+            const int i = I * kTile + lane;
+            const bool iv = i < N;
+            const double4 xi = iv ? x4[i] : zero4;
+#pragma unroll 4
+            for (int kk = 0; kk < kTile; ++kk) {
+                const bool v = iv && (K * kTile + kk < N) && (I != K || lane < kk);
+                const double dx = xi.x - sm.sK[kk].x;
+                const double dy = xi.y - sm.sK[kk].y;
+                const double dz = xi.z - sm.sK[kk].z;
+                const double b = dx * dx + dy * dy + dz * dz;
+                sm.bw[warp][kk][lane] = make_double2(v ? b : 1.0, v ? inv_pow52d(b) : 0.0);
+            }
+            __syncwarp();
+            double acc[kTile];
+#pragma unroll
+            for (int kk = 0; kk < kTile; ++kk) acc[kk] = 0.0;
+            double acc_i = 0.0;
+#pragma unroll 1
+            for (int jj = 0; jj < kTile; ++jj) {
+                const int j = J * kTile + jj;
+                const bool v = iv && (j < N) && (I != J || lane < jj);
+                const double dx = xi.x - sm.sJ[jj].x;
+                const double dy = xi.y - sm.sJ[jj].y;
+                const double dz = xi.z - sm.sJ[jj].z;
+                double c = dx * dx + dy * dy + dz * dz;
+                const double C = v ? inv_pow52d(c) : 0.0;
+                c = v ? c : 1.0;
+                const double ncc = -c * c, c375 = 0.375 * c;
+                double s = 0.0;
+#pragma unroll
+                for (int kk = 0; kk < kTile; ++kk) {
+                    const double2 aA = sm.tab[jj][kk];
+                    const double2 bB = sm.bw[warp][kk][lane];
+                    const double d = aA.x - bB.x;
+                    const double e = aA.x + bB.x;
+                    const double uv = fma(d, d, ncc);
+                    const double w = fma(e, -0.375, c375);
+                    const double P = uv * w;
+                    const double n = fma(aA.x, bB.x * c, P);
+                    const double ABC = aA.y * (bB.y * C);
+                    s = fma(n, ABC, s);
+                    acc[kk] = fma(n, ABC, acc[kk]);
+                }
+                acc_i += s;
+                sm.red[warp][jj][lane] = s;
+            }
+            __syncwarp();
+            double sj = 0.0;
+            for (int m = 0; m < kTile; ++m) sj += sm.red[warp][lane][m];
+            run_j += sj;
+            __syncwarp();
+#pragma unroll
+            for (int kk = 0; kk < kTile; ++kk) sm.red[warp][kk][lane] = acc[kk];
+            __syncwarp();
+            double sk = 0.0;
+            for (int m = 0; m < kTile; ++m) sk += sm.red[warp][lane][m];
+            run_k += sk;
+            __syncwarp();
+            if (iv) atomicAdd(&phi[i], acc_i);
+        }
+        sm.wsum[0][warp][lane] = run_j;
+        sm.wsum[1][warp][lane] = run_k;
+        __syncthreads();
+        if (warp < 2) {
+            double tot = 0.0;
+            for (int w = 0; w < kWarps64; ++w) tot += sm.wsum[warp][w][lane];
+            const int idx = (warp == 0 ? J : K) * kTile + lane;
+            if (idx < N) atomicAdd(&phi[idx], tot);
+        }
+        __syncthreads();
+    }
+}
+
+int grid_for(const void* kernel, int threads, size_t smem, int num_sms, long long items) {
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    long long g = (long long)per_sm * (num_sms > 0 ? num_sms : 1);
+    if (g > items) g = items;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t launch_pack_hilo(const double* X, int64_t N, float4* xhi, float4* xlo, int* flags,
+                             cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    const int threads = 256;
+    const long long blocks = (N + threads - 1) / threads;
+    pack_hilo_kernel<<<(unsigned)(blocks < 65535 ? blocks : 65535), threads, 0, s>>>(X, N, xhi, xlo,
+                                                                                    flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_f64(const double* X, int64_t N, double4* x4, int* flags, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    const int threads = 256;
+    const long long blocks = (N + threads - 1) / threads;
+    pack_f64_kernel<<<(unsigned)(blocks < 65535 ? blocks : 65535), threads, 0, s>>>(X, N, x4, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exh_fp32(const float4* xhi, const float4* xlo, int64_t N, double* phi,
+                            unsigned long long* counter, int* flags, int num_sms,
+                            cudaStream_t s) {
+    const int NT = (int)((N + kTile - 1) / kTile);
+    const long long items = (long long)NT * (NT + 1) / 2;
+    const int threads = kWarps32 * 32;
+    const size_t smem = sizeof(Fp32Smem);
+    cudaError_t e = cudaFuncSetAttribute((const void*)exh_fp32_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for((const void*)exh_fp32_kernel, threads, smem, num_sms, items);
+    exh_fp32_kernel<<<grid, threads, smem, s>>>(xhi, xlo, (int)N, NT, items, counter, phi, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exh_fp64(const double4* x4, int64_t N, double* phi, unsigned long long* counter,
+                            int* flags, int num_sms, cudaStream_t s) {
+    const int NT = (int)((N + kTile - 1) / kTile);
+    const long long items = (long long)NT * (NT + 1) / 2;
+    const int threads = kWarps64 * 32;
+    const size_t smem = sizeof(Fp64Smem);
+    cudaError_t e = cudaFuncSetAttribute((const void*)exh_fp64_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for((const void*)exh_fp64_kernel, threads, smem, num_sms, items);
+    exh_fp64_kernel<<<grid, threads, smem, s>>>(x4, (int)N, NT, items, counter, phi, flags);
+    return cudaGetLastError();
+}

@@ -1,0 +1,9 @@
+// Internal interface between the ABI dispatcher and the tree path.
+#pragma once
+
+#include "mbm_internal.h"
+
+// Multi-tree approximation of Phi (Algorithm 2 with the rules of Sec. 4).
+mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double eps, double alpha,
+                              bool absolute, const mbm_config& cfg, mbm_tree* tree, double* phi,
+                              mbm_stats* stats, cudaStream_t s);

@@ -1,0 +1,187 @@
+// FP32-bulk evaluation of all point triples of a tile triple (I, J, K).
+//
+// phi(x_i, x_j, x_k) = (1 + 3 cos t_i cos t_j cos t_k) / (r_ij r_ik r_jk)^3   (Sec. 1)
+//
+// With unit edge vectors e_ij = (x_j - x_i)/r_ij, e_ik, e_jk:
+//   cos t_i = e_ij . e_ik,  cos t_j = -e_ij . e_jk,  cos t_k = e_ik . e_jk,
+// so phi = (1 - 3 p1 p2 p3) rho_ij rho_ik rho_jk, p1 = e_ij.e_ik, p2 = e_ij.e_jk,
+// p3 = e_ik.e_jk, rho = r^-3. No squared lengths are subtracted, so a triangle
+// with one short side keeps full FP32 relative accuracy in every term.
+//
+// Loop structure: a lane owns particle i of tile I. (j,k) quantities come from
+// a shared-memory table built once per (J, K); (i,k) quantities are held in
+// registers for one half (16 columns) of K; (i,j) quantities are formed per j.
+// Per pair of triples (packed f32x2): 9 for the three dot products, 2 for
+// p1 p2 p3, 1 for n = 1 - 3t, 1 for rho_ik rho_jk, 1 for the row sum, 1 for
+// the full product, 1 for the column sum: 16 operations per triple, 9 of
+// them FMA -> 25 FLOPs per triple (FMA = 2).
+#pragma once
+
+#include "device_math.cuh"
+
+namespace mbm_tile {
+
+constexpr int kTile = 32;
+constexpr int kHalf = 16;   // K columns held in registers at once
+constexpr int kPairs = 8;   // f32x2 column pairs per half
+
+// Table entry for two adjacent columns k, k+1 of row j.
+struct __align__(16) TabPair {
+    float4 xy;  // (ex_k, ex_k+1, ey_k, ey_k+1)
+    float4 zr;  // (ez_k, ez_k+1, rho_k, rho_k+1)
+};
+
+struct PairF {
+    float ex, ey, ez, rho;
+};
+
+// Unit vector from p to q and rho = |q - p|^-3, from hi/lo coordinates.
+// rsqrt is refined by one Newton step (y <- y + y (1 - s y^2)/2, residual by
+// FMA); rho = y^3 is refined by one Newton step for rho^-2 = s^3
+// (rho <- rho + rho (1 - s^3 rho^2)/2). Returns s in *s_out (0 = coincident).
+__device__ __forceinline__ PairF pair_unit(float4 ph, float4 pl, float4 qh, float4 ql,
+                                           float* s_out) {
+    const float dx = (qh.x - ph.x) + (ql.x - pl.x);
+    const float dy = (qh.y - ph.y) + (ql.y - pl.y);
+    const float dz = (qh.z - ph.z) + (ql.z - pl.z);
+    const float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    float y = rsqrtf(s);
+    const float h = s * y;
+    y = fmaf(0.5f * y, fmaf(-h, y, 1.0f), y);
+    float rho = y * y * y;
+    const float q = s * rho;
+    rho = fmaf(0.5f * rho, fmaf(-q * q, s, 1.0f), rho);
+    *s_out = s;
+    PairF r;
+    r.ex = dx * y;
+    r.ey = dy * y;
+    r.ez = dz * y;
+    r.rho = rho;
+    return r;
+}
+
+// Build row j's entries of the (j,k) table (all k of the K tile). valid(j,k)
+// masked entries get rho = 0 so every triple through them contributes 0.
+// Returns true if some valid pair is coincident.
+__device__ __forceinline__ bool build_table_entry(TabPair (*tab)[kTile / 2], int jj, int kk,
+                                                  float4 jh, float4 jl, float4 kh, float4 kl,
+                                                  bool valid) {
+    float s = 1.f;
+    PairF p = pair_unit(jh, jl, kh, kl, &s);
+    bool bad = false;
+    if (!valid) {
+        p.ex = p.ey = p.ez = 0.f;
+        p.rho = 0.f;
+    } else if (!(s > 0.f)) {
+        bad = true;
+        p.ex = p.ey = p.ez = 0.f;
+        p.rho = 0.f;
+    }
+    float* xy = reinterpret_cast<float*>(&tab[jj][kk >> 1].xy);
+    float* zr = reinterpret_cast<float*>(&tab[jj][kk >> 1].zr);
+    const int o = kk & 1;
+    xy[o] = p.ex;
+    xy[2 + o] = p.ey;
+    zr[o] = p.ez;
+    zr[2 + o] = p.rho;
+    return bad;
+}
+
+// All triples of one I tile against the table (J rows x K columns).
+//   ih, il         : lane's particle (hi/lo); iv: lane holds a particle
+//   sJh/sJl, sKh/sKl: tile coordinates in shared memory
+//   nJ             : valid rows; the K validity is already in the table
+//   maskIJ         : require lane < jj  (I == J);  maskIK: lane < kk (I == K)
+//   redJ[jj][lane] : receives the lane's row sums (sum over k) for each j
+//   redK[kk][lane] : receives the lane's column sums (sum over j) for each k
+// Returns the lane's total (its particle's share).
+__device__ __forceinline__ float tile_triples(const TabPair (*tab)[kTile / 2], const float4* sJh,
+                                              const float4* sJl, const float4* sKh,
+                                              const float4* sKl, float4 ih, float4 il, bool iv,
+                                              int lane, int nJ, int nK, bool maskIJ, bool maskIK,
+                                              float (*redJ)[kTile + 1], float (*redK)[kTile + 1]) {
+    float acc_i = 0.f;
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const int kb = half * kHalf;
+        float2 vx[kPairs], vy[kPairs], vz[kPairs], rk[kPairs], acc[kPairs];
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+            float e[2][4];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int kk = kb + 2 * p + q;
+                float s;
+                const PairF pr = pair_unit(ih, il, sKh[kk], sKl[kk], &s);
+                const bool v = iv && kk < nK && (!maskIK || lane < kk) && s > 0.f;
+                e[q][0] = v ? pr.ex : 0.f;
+                e[q][1] = v ? pr.ey : 0.f;
+                e[q][2] = v ? pr.ez : 0.f;
+                e[q][3] = v ? pr.rho : 0.f;
+            }
+            vx[p] = make_float2(e[0][0], e[1][0]);
+            vy[p] = make_float2(e[0][1], e[1][1]);
+            vz[p] = make_float2(e[0][2], e[1][2]);
+            rk[p] = make_float2(e[0][3], e[1][3]);
+            acc[p] = make_float2(0.f, 0.f);
+        }
+        const float2 m3 = f2_splat(-3.0f), one = f2_splat(1.0f);
+#pragma unroll 1
+        for (int jj = 0; jj < kTile; ++jj) {
+            float s;
+            const PairF pu = pair_unit(ih, il, sJh[jj], sJl[jj], &s);
+            const bool v = iv && jj < nJ && (!maskIJ || lane < jj) && s > 0.f;
+            const float2 ux = f2_splat(v ? pu.ex : 0.f);
+            const float2 uy = f2_splat(v ? pu.ey : 0.f);
+            const float2 uz = f2_splat(v ? pu.ez : 0.f);
+            const float rij = v ? pu.rho : 0.f;
+            const float2 rij2 = f2_splat(rij);
+            float2 s2 = make_float2(0.f, 0.f);
+            const TabPair* row = tab[jj] + (kb >> 1);
+#pragma unroll
+            for (int p = 0; p < kPairs; ++p) {
+                const float4 t0 = row[p].xy;
+                const float4 t1 = row[p].zr;
+                const float2 wx = make_float2(t0.x, t0.y);
+                const float2 wy = make_float2(t0.z, t0.w);
+                const float2 wz = make_float2(t1.x, t1.y);
+                const float2 rjk = make_float2(t1.z, t1.w);
+                float2 p1 = f2_mul(ux, vx[p]);
+                p1 = f2_fma(uy, vy[p], p1);
+                p1 = f2_fma(uz, vz[p], p1);
+                float2 p2 = f2_mul(ux, wx);
+                p2 = f2_fma(uy, wy, p2);
+                p2 = f2_fma(uz, wz, p2);
+                float2 p3 = f2_mul(vx[p], wx);
+                p3 = f2_fma(vy[p], wy, p3);
+                p3 = f2_fma(vz[p], wz, p3);
+                const float2 t = f2_mul(f2_mul(p1, p2), p3);
+                const float2 n = f2_fma(t, m3, one);           // 1 + 3 cos cos cos
+                const float2 r2 = f2_mul(rk[p], rjk);          // rho_ik rho_jk
+                s2 = f2_fma(n, r2, s2);                        // row sum (x rho_ij later)
+                acc[p] = f2_fma(n, f2_mul(r2, rij2), acc[p]);  // column sums
+            }
+            const float srow = (s2.x + s2.y) * rij;
+            acc_i += srow;
+            if (half == 0) redJ[jj][lane] = srow;
+            else redJ[jj][lane] += srow;
+        }
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+            redK[kb + 2 * p][lane] = acc[p].x;
+            redK[kb + 2 * p + 1][lane] = acc[p].y;
+        }
+    }
+    __syncwarp();
+    return acc_i;
+}
+
+// Sum of row `r` of a 32 x 33 reduction buffer (one lane per row).
+__device__ __forceinline__ float row_sum(const float (*red)[kTile + 1], int r) {
+    float s = 0.f;
+#pragma unroll 8
+    for (int m = 0; m < kTile; ++m) s += red[r][m];
+    return s;
+}
+
+}  // namespace mbm_tile
