@@ -165,6 +165,28 @@ mbm_status mbm_forces(mbm_ctx* ctx, const double* X_dev, int64_t N, double eps, 
 mbm_status mbm_potential_vjp(mbm_ctx* ctx, const double* X_dev, int64_t N, const double* g_dev,
                              int mode, double* gradX_dev, mbm_stream_t stream);
 
+/*
+ * Exhaustive FP32-bulk Phi (as mbm_potential with MBM_EXH_FP32) for callers
+ * that cannot let a library allocate device memory: applications that own
+ * every device byte through their own pool or budget, loops that cannot
+ * afford the synchronisation an allocation or free brings, or plugins in a
+ * process that forbids foreign allocations. The paper has no counterpart;
+ * this is a deployment variant of the exhaustive sum.
+ *   X_dev   : N x 3 FP64 device array (current device), read only.
+ *   phi_dev : N FP64 device array, written.
+ *   N       : 0 <= N <= 65536; larger N returns MBM_EINVAL (use mbm_potential).
+ * No device memory is allocated or freed: scratch is a fixed 2 MiB + 256 B
+ * file-scope device array that every GPU loading the library holds until
+ * exit. The first call on a device resolves that array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture. Every call shares the one array, so calls whose work
+ * overlaps on the GPU (different streams, or concurrent host threads) race;
+ * serialise them. No input validation on the device: non-finite or
+ * coincident points give non-finite results rather than MBM_EINVAL.
+ */
+mbm_status mbm_potential_fp32_noalloc(const double* X_dev, int64_t N, double* phi_dev,
+                                      mbm_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

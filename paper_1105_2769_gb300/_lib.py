@@ -68,6 +68,7 @@ SIGNATURES = {
                                   _vp, _vp]),
     "mbm_forces": (_int, [_vp, _vp, _i64, _dbl, _dbl, _int, _vp, _vp]),
     "mbm_potential_vjp": (_int, [_vp, _vp, _i64, _vp, _int, _vp, _vp]),
+    "mbm_potential_fp32_noalloc": (_int, [_vp, _i64, _vp, _vp]),
 }
 OPTIONAL = {}
 
