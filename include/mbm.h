@@ -60,14 +60,18 @@ enum {
 
 /* Tuning and semantics of the tree path (Sec. 3-4). */
 typedef struct {
-    double tau;        /* absolute error term of Def. 2.3 (0 = pure relative) */
-    int32_t leaf_size; /* leaf threshold of Algorithm 1 (default 32, max 32) */
-    int32_t m_limit;   /* Monte Carlo sample cap of Algorithm 4 (default 256) */
-    double zeta;       /* speed-up factor of Algorithm 3 (default 4) */
-    uint64_t seed;     /* Philox key for Monte Carlo draws */
-    int32_t mc_rule;   /* 0 = relative stop test with T_i on both terms, 1 = as printed */
-    int32_t validate;  /* 1: synchronise and report non-finite/coincident input */
-    int32_t reserved[6];
+    double tau;          /* absolute error term of Def. 2.3 (0 = pure relative) */
+    int32_t leaf_size;   /* leaf threshold of Algorithm 1 (default 32, range 2..32) */
+    int32_t m_limit;     /* Monte Carlo sample cap of Algorithm 4 (default 256, <= 65535) */
+    double zeta;         /* speed-up factor of Algorithm 3 (default 4) */
+    uint64_t seed;       /* Philox-4x32-10 key for Monte Carlo draws */
+    int32_t mc_rule;     /* 0 = relative stop test with T_i on both terms, 1 = as printed */
+    int32_t validate;    /* 1: synchronise and report non-finite/coincident input */
+    int32_t seed_levels; /* Phi^l seed node = ancestor this many levels above a leaf (default 2) */
+    int32_t reserved0;
+    int64_t* tuple_counts; /* optional device int64[N]: point triples credited to each
+                              particle by prunes and base cases (validation; NULL = off) */
+    int32_t reserved[4];
 } mbm_config;
 
 /* Counters of the last solve (tree path); all zero for exhaustive modes. */
@@ -145,6 +149,34 @@ mbm_status mbm_potential_ex(mbm_ctx* ctx, const double* X_dev, int64_t N, double
 mbm_status mbm_potential_host(mbm_ctx* ctx, const double* X_host, int64_t N, double eps,
                               double alpha, int mode, const mbm_config* cfg,
                               double* phi_host, mbm_stream_t stream);
+
+/*
+ * Build the spatial tree of Sec. 3 (bottom-up phase) for X_dev (N x 3 FP64,
+ * device): Morton-ordered permutation, balanced node ranges of at most
+ * cfg->leaf_size points, FP64 bounding boxes and centres of mass, and the
+ * Phi^l seed of every node. The tree copies what it needs from X_dev and is
+ * owned by the caller (mbm_tree_free). Asynchronous on `stream` except for
+ * one size read-back. Errors: MBM_EINVAL (N < 3, bad leaf_size), MBM_EBUDGET,
+ * MBM_ENOMEM.
+ */
+mbm_status mbm_tree_build(mbm_ctx* ctx, const double* X_dev, int64_t N, const mbm_config* cfg,
+                          mbm_stream_t stream, mbm_tree** out);
+
+/* Release a tree (synchronises its device). */
+mbm_status mbm_tree_free(mbm_tree* tree);
+
+/* Number of nodes and leaves of a tree (for inspection). */
+mbm_status mbm_tree_info(const mbm_tree* tree, int64_t* n_nodes, int64_t* n_leaves,
+                         int32_t* depth);
+
+/* Copy a tree's layout to caller-owned device arrays (any may be NULL):
+ * perm_dev (int64[N], sorted position -> original index), lo_dev/hi_dev
+ * (FP64[3 * n_nodes], boxes), cen_dev (FP64[3 * n_nodes], centres of mass),
+ * phil_dev (FP64[n_nodes], Phi^l seed). Nodes are in heap order (root 0,
+ * children 2v+1, 2v+2). Asynchronous on `stream`. */
+mbm_status mbm_tree_export(const mbm_tree* tree, int64_t* perm_dev, double* lo_dev,
+                           double* hi_dev, double* cen_dev, double* phil_dev,
+                           mbm_stream_t stream);
 
 /*
  * Forces F_i = -dE/dx_i of the total energy E = sum_{a<b<c} phi_abc

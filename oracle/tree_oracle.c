@@ -429,7 +429,7 @@ static int try_summarize(osolve* S, const int64_t P[3]) {
     if (S->alpha > 0.0) {
         double tmin = T[0];
         for (int s = 1; s < 3; ++s) if (T[s] < tmin) tmin = T[s];
-        if (S->zeta * S->m_limit <= tmin) {
+        if (tmin >= 1.0 && S->zeta * S->m_limit <= tmin) { /* every slot has tuples to draw */
             S->mc_attempts++;
             int64_t total = 0;
             for (int s = 0; s < 3; ++s) if (first[s]) total += node_n(t, P[s]);

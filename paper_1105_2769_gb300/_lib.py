@@ -30,7 +30,9 @@ class Config(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("leaf_size", ctypes.c_int32),
                 ("m_limit", ctypes.c_int32), ("zeta", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("mc_rule", ctypes.c_int32),
-                ("validate", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("validate", ctypes.c_int32), ("seed_levels", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("tuple_counts", ctypes.c_void_p),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class Stats(ctypes.Structure):
@@ -69,6 +71,11 @@ SIGNATURES = {
     "mbm_forces": (_int, [_vp, _vp, _i64, _dbl, _dbl, _int, _vp, _vp]),
     "mbm_potential_vjp": (_int, [_vp, _vp, _i64, _vp, _int, _vp, _vp]),
     "mbm_potential_fp32_noalloc": (_int, [_vp, _i64, _vp, _vp]),
+    "mbm_tree_build": (_int, [_vp, _vp, _i64, ctypes.POINTER(Config), _vp, ctypes.POINTER(_vp)]),
+    "mbm_tree_free": (_int, [_vp]),
+    "mbm_tree_info": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                             ctypes.POINTER(ctypes.c_int32)]),
+    "mbm_tree_export": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 OPTIONAL = {}
 

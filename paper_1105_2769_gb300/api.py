@@ -95,15 +95,77 @@ def _stream_handle() -> ctypes.c_void_p:
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+class Tree:
+    """A built spatial tree (mbm_tree) for one point set; reusable across solves."""
+
+    def __init__(self, X: torch.Tensor, config: _lib.Config | None = None,
+                 ctx: Context | None = None):
+        X = _check_points(X)
+        self.ctx = ctx or default_context(X.device.index)
+        cfg = config if config is not None else _lib.default_config()
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().mbm_tree_build(self.ctx.handle, ctypes.c_void_p(X.data_ptr()),
+                                              X.shape[0], ctypes.byref(cfg), _stream_handle(),
+                                              ctypes.byref(h)))
+        self.handle = h
+        self.n = X.shape[0]
+        self.device = X.device
+
+    def info(self):
+        nn, nl, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _lib.check(_lib.load().mbm_tree_info(self.handle, ctypes.byref(nn), ctypes.byref(nl),
+                                             ctypes.byref(d)))
+        return {"n_nodes": nn.value, "n_leaves": nl.value, "depth": d.value}
+
+    def export(self):
+        """perm, node boxes, centres and Phi^l as CPU numpy arrays."""
+        m = self.info()["n_nodes"]
+        perm = torch.empty(self.n, dtype=torch.int64, device=self.device)
+        lo = torch.empty((m, 3), dtype=torch.float64, device=self.device)
+        hi = torch.empty_like(lo)
+        cen = torch.empty_like(lo)
+        phil = torch.empty(m, dtype=torch.float64, device=self.device)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+        _lib.check(_lib.load().mbm_tree_export(self.handle, ptr(perm), ptr(lo), ptr(hi), ptr(cen),
+                                               ptr(phil), _stream_handle()))
+        torch.cuda.synchronize(self.device)
+        return {k: v.cpu().numpy() for k, v in
+                dict(perm=perm, lo=lo, hi=hi, cen=cen, phil=phil).items()}
+
+    def close(self):
+        if self.handle:
+            _lib.load().mbm_tree_free(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tree_config(**kw) -> _lib.Config:
+    """Default mbm_config with fields overridden (tau, leaf_size, m_limit, zeta,
+    seed, mc_rule, validate, seed_levels)."""
+    return _lib.default_config(**kw)
+
+
 def potential(X: torch.Tensor, eps: float = 0.0, alpha: float = 0.0, mode="fp32",
               config: _lib.Config | None = None, tree=None, stats: bool = False,
-              ctx: Context | None = None, out: torch.Tensor | None = None):
-    """Phi(x_i) for every particle (Eq. 1 with the Axilrod-Teller phi)."""
+              ctx: Context | None = None, out: torch.Tensor | None = None,
+              tuple_counts: torch.Tensor | None = None):
+    """Phi(x_i) for every particle (Eq. 1 with the Axilrod-Teller phi).
+
+    tuple_counts: optional int64 CUDA tensor (N,) that receives, in tree
+    modes, the number of point triples credited to each particle."""
     X = _check_points(X)
     n = X.shape[0]
     ctx = ctx or default_context(X.device.index)
     phi = out if out is not None else torch.empty(n, dtype=torch.float64, device=X.device)
     cfg = config if config is not None else _lib.default_config()
+    if tuple_counts is not None:
+        cfg = _lib.Config.from_buffer_copy(cfg)
+        cfg.tuple_counts = tuple_counts.data_ptr()
     st = _lib.Stats()
     L = _lib.load()
     _lib.check(L.mbm_potential_ex(ctx.handle, ctypes.c_void_p(X.data_ptr()), n, float(eps),

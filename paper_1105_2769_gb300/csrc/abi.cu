@@ -39,6 +39,8 @@ extern "C" void mbm_config_default(mbm_config* cfg) {
     cfg->seed = 0x5eed5eedULL;
     cfg->mc_rule = 0;
     cfg->validate = 1;
+    cfg->seed_levels = 2;
+    cfg->tuple_counts = nullptr;
 }
 
 mbm_status mbm_budget_charge(mbm_ctx* ctx, size_t bytes) {

@@ -1,7 +1,1385 @@
-// Multi-tree approximation (Algorithm 2 with the p = 0 rules of Sec. 4).
-#include "mbm_tree_api.h"
+// Multi-tree approximation of Phi on the GPU (Algorithm 2 with the p = 0 and
+// Monte Carlo rules of Sec. 4).
+//
+//   a4 tree build   : bounding cube -> 63-bit Morton keys (2^21 grid) -> radix
+//                     sort (ties by index) -> balanced ranges halved to <= leaf
+//                     size; FP64 boxes, centres of mass, squared diameters.
+//   seed            : Phi^l (Sec. 4 summary statistic, read as a lower bound on
+//                     |Phi|): |exact sum over each particle's seed node|, min
+//                     over every node (Sec. 5: Phi^l(P) = min over children).
+//   a5/a6 traversal : breadth-first over node triples from (root, root, root);
+//                     per triple the p = 0 interval bound, T_i of Fig. 4 and
+//                     the budget of Eq. (deterministic_prune) decide: prune
+//                     (accumulate T_i phi(c1,c2,c3) per node), Monte Carlo
+//                     candidate, base case, or split the largest-diameter
+//                     node (all of its copies; non-decreasing child triples).
+//   a7 Monte Carlo  : Algorithms 3-5; a lane per particle draws tuples with
+//                     Philox-4x32-10, FP32 phi, FP64 Welford statistics and
+//                     stop test; a triple passes only if all its particles do.
+//   a8 base cases   : exhaustive leaf triples with the Fig. 4 masks, FP32 bulk
+//                     (tile_fp32.cuh), FP64 accumulation.
+//   a9 top-down     : node accumulators summed along each leaf's root path.
+//
+// Every decision is computed in FP64 in the same operation order as the
+// serial restatement (explicit round-to-nearest intrinsics, no contraction),
+// and Phi^l is fixed before the traversal, so the breadth-first order makes
+// the same decisions as a depth-first recursion.
+#include <cub/cub.cuh>
 
-mbm_status mbm_tree_potential(mbm_ctx*, const double*, int64_t, double, double, bool,
-                              const mbm_config&, mbm_tree*, double*, mbm_stats*, cudaStream_t) {
-    return mbm_fail(MBM_ENOTSUP, "tree path not built yet");
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mbm_tree_api.h"
+#include "tile_fp32.cuh"
+
+struct mbm_tree {
+    mbm_ctx* ctx = nullptr;
+    int device = 0;
+    int64_t N = 0;
+    int leaf_size = 32;
+    int depth = 0;
+    int64_t n_nodes = 0, n_leaves = 0;
+    int seed_levels = 2;
+    void* mem = nullptr;
+    size_t bytes = 0;
+    int64_t* perm = nullptr;  // sorted position -> original index
+    double* xs = nullptr;     // sorted coordinates, 3 per particle
+    float4* xh = nullptr;     // sorted hi/lo FP32 coordinates
+    float4* xl = nullptr;
+    double* nlo = nullptr;    // per node, 3 each
+    double* nhi = nullptr;
+    double* ncen = nullptr;
+    double* ndiam2 = nullptr; // per node
+    double* nphil = nullptr;  // per node
+};
+
+namespace {
+
+using mbm_tile::kTile;
+using ull = unsigned long long;
+
+// ---------------------------------------------------------------------------
+// Node geometry helpers (implicit complete binary tree in heap order).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ void node_range(int64_t v, int64_t N, int64_t& b, int64_t& e) {
+#ifdef __CUDA_ARCH__
+    const int d = 63 - __clzll((long long)(v + 1));
+#else
+    int d = 0;
+    while ((v + 1) >> (d + 1)) ++d;
+#endif
+    const int64_t q = v + 1 - ((int64_t)1 << d);
+    b = (q * N) >> d;
+    e = ((q + 1) * N) >> d;
+}
+
+int tree_depth(int64_t N, int leaf) {
+    int d = 0;
+    while (((N + ((int64_t)1 << d) - 1) >> d) > leaf) ++d;
+    return d;
+}
+
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t r = 0;
+#pragma unroll
+    for (int b = 0; b < 21; ++b) r |= (uint64_t)((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// a4: build.
+// ---------------------------------------------------------------------------
+__global__ void bbox_partial_kernel(const double* __restrict__ X, int64_t N, double* part) {
+    __shared__ double s[6][256];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            const double x = X[3 * i + k];
+            lo[k] = fmin(lo[k], x);
+            hi[k] = fmax(hi[k], x);
+        }
+    for (int k = 0; k < 3; ++k) {
+        s[k][threadIdx.x] = lo[k];
+        s[3 + k][threadIdx.x] = hi[k];
+    }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int k = 0; k < 3; ++k) {
+                s[k][threadIdx.x] = fmin(s[k][threadIdx.x], s[k][threadIdx.x + o]);
+                s[3 + k][threadIdx.x] = fmax(s[3 + k][threadIdx.x], s[3 + k][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) part[6 * blockIdx.x + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void bbox_final_kernel(const double* part, int nb, double* box) {
+    if (threadIdx.x >= 6) return;
+    const int k = threadIdx.x;
+    double v = part[k];
+    for (int b = 1; b < nb; ++b) v = k < 3 ? fmin(v, part[6 * b + k]) : fmax(v, part[6 * b + k]);
+    box[k] = v;
+}
+
+__global__ void morton_kernel(const double* __restrict__ X, int64_t N, const double* box,
+                              uint64_t* keys, int* idx, int* flags) {
+    const double l0 = box[0], l1 = box[1], l2 = box[2];
+    double ext = __dsub_rn(box[3], l0);
+    if (__dsub_rn(box[4], l1) > ext) ext = __dsub_rn(box[4], l1);
+    if (__dsub_rn(box[5], l2) > ext) ext = __dsub_rn(box[5], l2);
+    const double scale = ext > 0.0 ? __ddiv_rn(2097152.0, ext) : 0.0;
+    const double lo[3] = {l0, l1, l2};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t key = 0;
+        for (int d = 0; d < 3; ++d) {
+            if (!isfinite(X[3 * i + d])) atomicOr(flags, MBM_FLAG_NONFINITE);
+            const double q = floor(__dmul_rn(__dsub_rn(X[3 * i + d], lo[d]), scale));
+            const uint32_t qi = q < 0.0 ? 0u : (q > 2097151.0 ? 2097151u : (uint32_t)q);
+            key |= spread3(qi) << d;
+        }
+        keys[i] = key;
+        idx[i] = (int)i;
+    }
+}
+
+__global__ void gather_kernel(const double* __restrict__ X, int64_t N, const int* __restrict__ sidx,
+                              int64_t* perm, double* xs, float4* xh, float4* xl) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = sidx[s];
+        perm[s] = o;
+        const double x = X[3 * o], y = X[3 * o + 1], z = X[3 * o + 2];
+        xs[3 * s] = x;
+        xs[3 * s + 1] = y;
+        xs[3 * s + 2] = z;
+        const float hx = (float)x, hy = (float)y, hz = (float)z;
+        xh[s] = make_float4(hx, hy, hz, 0.f);
+        xl[s] = make_float4((float)(x - (double)hx), (float)(y - (double)hy),
+                            (float)(z - (double)hz), 0.f);
+    }
+}
+
+// One warp per leaf: box, coordinate sums.
+__global__ void leaf_stats_kernel(const double* __restrict__ xs, int64_t N, int64_t first_leaf,
+                                  int64_t n_leaves, double* nlo, double* nhi, double* nsum) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (w >= n_leaves) return;
+    const int64_t v = first_leaf + w;
+    int64_t b, e;
+    node_range(v, N, b, e);
+    double lo[3], hi[3], sm[3];
+    for (int k = 0; k < 3; ++k) {
+        const bool in = b + lane < e;
+        const double x = in ? xs[3 * (b + lane) + k] : 0.0;
+        lo[k] = in ? x : INFINITY;
+        hi[k] = in ? x : -INFINITY;
+        sm[k] = x;
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+            sm[k] += __shfl_xor_sync(0xffffffffu, sm[k], o);
+        }
+    if (lane < 3) {
+        nlo[3 * v + lane] = lane == 0 ? lo[0] : (lane == 1 ? lo[1] : lo[2]);
+        nhi[3 * v + lane] = lane == 0 ? hi[0] : (lane == 1 ? hi[1] : hi[2]);
+        nsum[3 * v + lane] = lane == 0 ? sm[0] : (lane == 1 ? sm[1] : sm[2]);
+    }
+}
+
+__global__ void internal_stats_kernel(int64_t first, int64_t count, double* nlo, double* nhi,
+                                      double* nsum) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t v = first + t, L = 2 * v + 1, R = 2 * v + 2;
+    for (int k = 0; k < 3; ++k) {
+        nlo[3 * v + k] = fmin(nlo[3 * L + k], nlo[3 * R + k]);
+        nhi[3 * v + k] = fmax(nhi[3 * L + k], nhi[3 * R + k]);
+        nsum[3 * v + k] = nsum[3 * L + k] + nsum[3 * R + k];
+    }
+}
+
+__global__ void node_finish_kernel(int64_t N, int64_t n_nodes, const double* nlo, const double* nhi,
+                                   double* ncen /* holds sums on entry */, double* ndiam2) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n_nodes) return;
+    int64_t b, e;
+    node_range(v, N, b, e);
+    const double cnt = (double)(e - b);
+    for (int k = 0; k < 3; ++k) ncen[3 * v + k] = cnt > 0 ? ncen[3 * v + k] / cnt : 0.0;
+    const double dx = __dsub_rn(nhi[3 * v], nlo[3 * v]);
+    const double dy = __dsub_rn(nhi[3 * v + 1], nlo[3 * v + 1]);
+    const double dz = __dsub_rn(nhi[3 * v + 2], nlo[3 * v + 2]);
+    ndiam2[v] = cnt > 0 ? __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz))
+                        : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Range triples (base cases and the Phi^l seed), one warp each, FP32 bulk.
+// ---------------------------------------------------------------------------
+struct WarpSmem {
+    mbm_tile::TabPair tab[kTile][kTile / 2];
+    float4 sJh[kTile], sJl[kTile], sKh[kTile], sKl[kTile];
+    float redJ[kTile][kTile + 1];
+    float redK[kTile][kTile + 1];
+};
+constexpr int kRangeWarps = 4;
+
+// All triples (i in R1, j in R2, k in R3) with i<j if R1 == R2, j<k if
+// R2 == R3 and i<k if R1 == R3; each credited to its three members in out[].
+__device__ void range_triple(WarpSmem& w, const float4* __restrict__ xh,
+                             const float4* __restrict__ xl, int64_t b1, int n1, int64_t b2, int n2,
+                             int64_t b3, int n3, bool e12, bool e23, bool e13, double* out,
+                             int* flags) {
+    const int lane = threadIdx.x & 31;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    w.sJh[lane] = lane < n2 ? xh[b2 + lane] : z4;
+    w.sJl[lane] = lane < n2 ? xl[b2 + lane] : z4;
+    w.sKh[lane] = lane < n3 ? xh[b3 + lane] : z4;
+    w.sKl[lane] = lane < n3 ? xl[b3 + lane] : z4;
+    __syncwarp();
+    bool bad = false;
+    for (int e = lane; e < kTile * kTile; e += 32) {
+        const int jj = e >> 5, kk = e & 31;
+        const bool v = jj < n2 && kk < n3 && (!e23 || jj < kk);
+        bad |= mbm_tile::build_table_entry(w.tab, jj, kk, w.sJh[jj], w.sJl[jj], w.sKh[kk],
+                                           w.sKl[kk], v);
+    }
+    if (bad) atomicOr(flags, MBM_FLAG_COINCIDENT);
+    __syncwarp();
+    const bool iv = lane < n1;
+    const float4 ih = iv ? xh[b1 + lane] : z4;
+    const float4 il = iv ? xl[b1 + lane] : z4;
+    const float acc_i = mbm_tile::tile_triples(w.tab, w.sJh, w.sJl, w.sKh, w.sKl, ih, il, iv, lane,
+                                               n2, n3, e12, e13, w.redJ, w.redK);
+    const float rj = mbm_tile::row_sum(w.redJ, lane);
+    const float rk = mbm_tile::row_sum(w.redK, lane);
+    if (lane < n2) atomicAdd(&out[b2 + lane], (double)rj);
+    if (lane < n3) atomicAdd(&out[b3 + lane], (double)rk);
+    if (iv) atomicAdd(&out[b1 + lane], (double)acc_i);
+    __syncwarp();
+}
+
+// Seed items: for each seed node A (level sd), chunk triples I <= J <= K of
+// its 32-point chunks. `combos` lists (I,J,K) for the maximum chunk count.
+__global__ void __launch_bounds__(kRangeWarps * 32)
+seed_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_t N, int sd,
+            int64_t n_seed_nodes, const int4* __restrict__ combos, int n_combos, double* seed,
+            int* flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem& w = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
+    const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (item >= n_seed_nodes * n_combos) return;
+    const int64_t a = item / n_combos;
+    const int4 c = combos[item % n_combos];
+    int64_t b, e;
+    node_range(((int64_t)1 << sd) - 1 + a, N, b, e);
+    const int64_t n = e - b;
+    const int chunks = (int)((n + kTile - 1) / kTile);
+    if (c.z >= chunks) return;  // warp-uniform
+    auto len = [&](int q) { const int64_t r = n - (int64_t)q * kTile; return (int)(r < kTile ? r : kTile); };
+    range_triple(w, xh, xl, b + (int64_t)c.x * kTile, len(c.x), b + (int64_t)c.y * kTile, len(c.y),
+                 b + (int64_t)c.z * kTile, len(c.z), c.x == c.y, c.y == c.z, c.x == c.z, seed,
+                 flags);
+}
+
+// Base cases: leaf triples from the traversal's base list.
+__global__ void __launch_bounds__(kRangeWarps * 32)
+base_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_t N,
+            const int4* __restrict__ items, int64_t n_items, double* acc, int* flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem& w = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
+    const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (item >= n_items) return;
+    const int4 t = items[item];
+    int64_t b1, e1, b2, e2, b3, e3;
+    node_range(t.x, N, b1, e1);
+    node_range(t.y, N, b2, e2);
+    node_range(t.z, N, b3, e3);
+    range_triple(w, xh, xl, b1, (int)(e1 - b1), b2, (int)(e2 - b2), b3, (int)(e3 - b3), t.x == t.y,
+                 t.y == t.z, t.x == t.z, acc, flags);
+}
+
+// Tuple counts of base cases by enumeration (validation only).
+__global__ void base_count_kernel(int64_t N, const int4* __restrict__ items, int64_t n_items,
+                                  unsigned long long* cnt) {
+    const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (item >= n_items) return;
+    const int4 t = items[item];
+    int64_t b1, e1, b2, e2, b3, e3;
+    node_range(t.x, N, b1, e1);
+    node_range(t.y, N, b2, e2);
+    node_range(t.z, N, b3, e3);
+    for (int64_t i = b1 + lane; i < e1; i += 32)
+        for (int64_t j = b2; j < e2; ++j) {
+            if (t.x == t.y && j <= i) continue;
+            for (int64_t k = b3; k < e3; ++k) {
+                if (t.y == t.z && k <= j) continue;
+                atomicAdd(&cnt[i], 1ULL);
+                atomicAdd(&cnt[j], 1ULL);
+                atomicAdd(&cnt[k], 1ULL);
+            }
+        }
+}
+
+// Phi^l per node: |seed| per particle, min over leaves, then up the tree.
+__global__ void phil_leaf_kernel(const double* __restrict__ seed, int64_t N, int64_t first_leaf,
+                                 int64_t n_leaves, double* nphil) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (w >= n_leaves) return;
+    const int64_t v = first_leaf + w;
+    int64_t b, e;
+    node_range(v, N, b, e);
+    double m = b + lane < e ? fabs(seed[b + lane]) : INFINITY;
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) nphil[v] = b < e ? m : 0.0;
+}
+
+__global__ void phil_internal_kernel(int64_t first, int64_t count, double* nphil) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t v = first + t;
+    nphil[v] = fmin(nphil[2 * v + 1], nphil[2 * v + 2]);
+}
+
+// ---------------------------------------------------------------------------
+// a5/a6: bound evaluator and traversal.
+// ---------------------------------------------------------------------------
+struct Trav {
+    int64_t N, n_nodes, n_leaves;
+    const double *nlo, *nhi, *ncen, *ndiam2, *nphil;
+    const double* xs;
+    const float4 *xh, *xl;
+    double eps, tau, troot, zeta, z, alpha;
+    int m_limit, mc_rule;
+    uint32_t key0, key1;
+    double* node_acc;
+    double* pt_acc;
+    ull* node_cnt;  // optional
+    ull* pt_cnt;    // optional
+    int4* next;
+    ull* n_next;
+    int64_t cap_next;
+    int4* mc;
+    ull* n_mc;
+    int64_t cap_mc;
+    int4* base;
+    ull* n_base;
+    int64_t cap_base;
+    int* flags;
+    ull* stat;  // visited, det, mc prunes, mc attempts, base, samples
+};
+
+__device__ __forceinline__ bool is_leaf(const Trav& p, int64_t v) {
+    return v >= p.n_nodes - p.n_leaves;
+}
+
+__device__ __forceinline__ double choose2(double n) {
+    return __dmul_rn(__dmul_rn(n, __dsub_rn(n, 1.0)), 0.5);
+}
+
+// T_i of Fig. 4 for the particle's slot.
+__device__ double tuples_for_slot(const int64_t P[3], const double n[3], int slot) {
+    const bool e01 = P[0] == P[1], e12 = P[1] == P[2];
+    if (e01 && e12) return choose2(__dsub_rn(n[0], 1.0));
+    if (e01) return slot == 2 ? choose2(n[0]) : __dmul_rn(__dsub_rn(n[0], 1.0), n[2]);
+    if (e12) return slot == 0 ? choose2(n[1]) : __dmul_rn(n[0], __dsub_rn(n[1], 1.0));
+    if (slot == 0) return __dmul_rn(n[1], n[2]);
+    if (slot == 1) return __dmul_rn(n[0], n[2]);
+    return __dmul_rn(n[0], n[1]);
+}
+
+// Squared minimum and maximum point distances between two boxes (Fig. 3).
+__device__ void box_d2(const Trav& p, int64_t a, int64_t b, double& dl, double& du) {
+    double l = 0.0, u = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        const double x = __dsub_rn(p.nlo[3 * b + k], p.nhi[3 * a + k]);
+        const double y = __dsub_rn(p.nlo[3 * a + k], p.nhi[3 * b + k]);
+        double g = x > y ? x : y;
+        if (g < 0.0) g = 0.0;
+        l = __dadd_rn(l, __dmul_rn(g, g));
+        const double c = __dsub_rn(p.nhi[3 * b + k], p.nlo[3 * a + k]);
+        const double e = __dsub_rn(p.nhi[3 * a + k], p.nlo[3 * b + k]);
+        const double m = c > e ? c : e;
+        u = __dadd_rn(u, __dmul_rn(m, m));
+    }
+    dl = l;
+    du = u;
+}
+
+__device__ void interval_mul(double a0, double a1, double b0, double b1, double& r0, double& r1) {
+    const double q[4] = {__dmul_rn(a0, b0), __dmul_rn(a0, b1), __dmul_rn(a1, b0), __dmul_rn(a1, b1)};
+    double lo = q[0], hi = q[0];
+    for (int i = 1; i < 4; ++i) {
+        if (q[i] < lo) lo = q[i];
+        if (q[i] > hi) hi = q[i];
+    }
+    r0 = lo;
+    r1 = hi;
+}
+
+// [phi_lo, phi_hi] over all point triples, from squared-distance intervals
+// c (slots 1-2), b (slots 1-3), a (slots 2-3): the cosine product by interval
+// arithmetic on (b+c-a)(a+c-b)(a+b-c)/(8abc) within [-1, 1/8], the distance
+// factor by its monotone bounds.
+__device__ void phi_interval(double cl, double cu, double bl, double bu, double al, double au,
+                             double& plo, double& phi) {
+    double Cl = -1.0, Ch = 0.125;
+    const double Dl = __dmul_rn(__dmul_rn(__dmul_rn(8.0, al), bl), cl);
+    const double Dh = __dmul_rn(__dmul_rn(__dmul_rn(8.0, au), bu), cu);
+    if (Dl > 0.0) {
+        const double U0 = __dsub_rn(__dadd_rn(bl, cl), au), U1 = __dsub_rn(__dadd_rn(bu, cu), al);
+        const double V0 = __dsub_rn(__dadd_rn(al, cl), bu), V1 = __dsub_rn(__dadd_rn(au, cu), bl);
+        const double W0 = __dsub_rn(__dadd_rn(al, bl), cu), W1 = __dsub_rn(__dadd_rn(au, bu), cl);
+        double p0, p1, q0, q1;
+        interval_mul(U0, U1, V0, V1, p0, p1);
+        interval_mul(p0, p1, W0, W1, q0, q1);
+        const double a0 = __ddiv_rn(q0, Dl), a1 = __ddiv_rn(q0, Dh);
+        const double c0 = __ddiv_rn(q1, Dl), c1 = __ddiv_rn(q1, Dh);
+        const double lo = a0 < a1 ? a0 : a1;
+        const double hi = c0 > c1 ? c0 : c1;
+        if (lo > Cl) Cl = lo;
+        if (hi < Ch) Ch = hi;
+        if (Cl > Ch) Cl = Ch;
+    }
+    const double nl = __dadd_rn(1.0, __dmul_rn(3.0, Cl));
+    const double nh = __dadd_rn(1.0, __dmul_rn(3.0, Ch));
+    const double Sl = __dmul_rn(__dmul_rn(al, bl), cl), Sh = __dmul_rn(__dmul_rn(au, bu), cu);
+    const double R3l = __dmul_rn(Sl, __dsqrt_rn(Sl)), R3h = __dmul_rn(Sh, __dsqrt_rn(Sh));
+    const double hiv = nh >= 0.0 ? (R3l > 0.0 ? __ddiv_rn(nh, R3l) : INFINITY) : __ddiv_rn(nh, R3h);
+    const double lov = nl >= 0.0 ? __ddiv_rn(nl, R3h) : (R3l > 0.0 ? __ddiv_rn(nl, R3l) : -INFINITY);
+    phi = __dadd_rn(hiv, __dmul_rn(fabs(hiv), 1e-13));
+    plo = __dsub_rn(lov, __dmul_rn(fabs(lov), 1e-13));
+}
+
+// phi at three points (FP64, law of cosines on squared sides).
+__device__ double phi_f64(const double* x, const double* y, const double* z) {
+    double c = 0, b = 0, a = 0;
+    for (int k = 0; k < 3; ++k) {
+        const double u = y[k] - x[k], v = z[k] - x[k], w = z[k] - y[k];
+        c += u * u;
+        b += v * v;
+        a += w * w;
+    }
+    const double P = (b + c - a) * (a + c - b) * (a + b - c);
+    const double S = a * b * c;
+    return (S + 0.375 * P) / (S * S * sqrt(S));
+}
+
+// Warp-aggregated append: returns this lane's first slot.
+__device__ __forceinline__ ull warp_append(ull* counter, int count) {
+    const int lane = threadIdx.x & 31;
+    int incl = count;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    ull base = 0;
+    if (lane == 31 && total > 0) base = atomicAdd(counter, (ull)total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + (ull)(incl - count);
+}
+
+// Children of a split (Algorithm 2 with all copies of the node split at once).
+__device__ int split_children(const Trav& p, const int64_t P[3], int4 out[4]) {
+    int ks = -1;
+    double best = -1.0;
+    for (int s = 0; s < 3; ++s) {
+        if (is_leaf(p, P[s])) continue;
+        const double d = p.ndiam2[P[s]];
+        if (d > best) {
+            best = d;
+            ks = s;
+        }
+    }
+    const int64_t v = P[ks], L = 2 * v + 1, R = 2 * v + 2;
+    const bool e01 = P[0] == P[1], e12 = P[1] == P[2];
+    if (e01 && e12) {
+        out[0] = make_int4((int)L, (int)L, (int)L, 0);
+        out[1] = make_int4((int)L, (int)L, (int)R, 0);
+        out[2] = make_int4((int)L, (int)R, (int)R, 0);
+        out[3] = make_int4((int)R, (int)R, (int)R, 0);
+        return 4;
+    }
+    if (e01 && ks <= 1) {
+        out[0] = make_int4((int)L, (int)L, (int)P[2], 0);
+        out[1] = make_int4((int)L, (int)R, (int)P[2], 0);
+        out[2] = make_int4((int)R, (int)R, (int)P[2], 0);
+        return 3;
+    }
+    if (e12 && ks >= 1) {
+        out[0] = make_int4((int)P[0], (int)L, (int)L, 0);
+        out[1] = make_int4((int)P[0], (int)L, (int)R, 0);
+        out[2] = make_int4((int)P[0], (int)R, (int)R, 0);
+        return 3;
+    }
+    int64_t A[3] = {P[0], P[1], P[2]}, B[3] = {P[0], P[1], P[2]};
+    A[ks] = L;
+    B[ks] = R;
+    out[0] = make_int4((int)A[0], (int)A[1], (int)A[2], 0);
+    out[1] = make_int4((int)B[0], (int)B[1], (int)B[2], 0);
+    return 2;
+}
+
+// Node sizes, T_i and distinct-slot flags of a triple.
+__device__ void triple_counts(const Trav& p, const int64_t P[3], double n[3], double T[3],
+                              bool first[3]) {
+    for (int s = 0; s < 3; ++s) {
+        int64_t b, e;
+        node_range(P[s], p.N, b, e);
+        n[s] = (double)(e - b);
+    }
+    for (int s = 0; s < 3; ++s) T[s] = tuples_for_slot(P, n, s);
+    first[0] = true;
+    first[1] = P[1] != P[0];
+    first[2] = P[2] != P[1];
+}
+
+enum : int { kActNone = 0, kActDet = 1, kActMC = 2, kActBase = 3, kActSplit = 4 };
+
+__global__ void classify_kernel(const int4* __restrict__ front, int64_t n_front, Trav p) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int act = kActNone;
+    int4 kids[4];
+    int n_kids = 0;
+    int4 me = make_int4(0, 0, 0, 0);
+    if (i < n_front) {
+        me = front[i];
+        const int64_t P[3] = {me.x, me.y, me.z};
+        double n[3], T[3];
+        bool first[3];
+        triple_counts(p, P, n, T, first);
+        double sl[3], sh[3];
+        box_d2(p, P[0], P[1], sl[0], sh[0]);
+        box_d2(p, P[0], P[2], sl[1], sh[1]);
+        box_d2(p, P[1], P[2], sl[2], sh[2]);
+        double plo, phi_hi;
+        phi_interval(sl[0], sh[0], sl[1], sh[1], sl[2], sh[2], plo, phi_hi);
+        const double width = __dsub_rn(phi_hi, plo);
+        const double amax = fabs(plo) > fabs(phi_hi) ? fabs(plo) : fabs(phi_hi);
+        double lb = INFINITY;
+        for (int s = 0; s < 3; ++s) {
+            if (!first[s]) continue;
+            const double v = __dsub_rn(p.nphil[P[s]], __dmul_rn(T[s], amax));
+            if (v < lb) lb = v;
+        }
+        const double budget =
+            __ddiv_rn(__dadd_rn(__dmul_rn(p.eps, lb > 0.0 ? lb : 0.0), p.tau), p.troot);
+        if (width <= budget) {
+            act = kActDet;
+            const double f = phi_f64(p.ncen + 3 * P[0], p.ncen + 3 * P[1], p.ncen + 3 * P[2]);
+            for (int s = 0; s < 3; ++s) {
+                if (!first[s]) continue;
+                atomicAdd(&p.node_acc[P[s]], T[s] * f);
+                if (p.node_cnt) atomicAdd(&p.node_cnt[P[s]], (ull)T[s]);
+            }
+        } else {
+            double tmin = T[0];
+            for (int s = 1; s < 3; ++s)
+                if (T[s] < tmin) tmin = T[s];
+            if (p.alpha > 0.0 && tmin >= 1.0 && __dmul_rn(p.zeta, (double)p.m_limit) <= tmin) {
+                act = kActMC;
+            } else if (is_leaf(p, P[0]) && is_leaf(p, P[1]) && is_leaf(p, P[2])) {
+                act = kActBase;
+            } else {
+                act = kActSplit;
+                n_kids = split_children(p, P, kids);
+            }
+        }
+    }
+    // statistics
+    const unsigned act_mask = __ballot_sync(0xffffffffu, act != kActNone);
+    const unsigned det_mask = __ballot_sync(0xffffffffu, act == kActDet);
+    const unsigned mc_mask = __ballot_sync(0xffffffffu, act == kActMC);
+    if ((threadIdx.x & 31) == 0) {
+        if (act_mask) atomicAdd(&p.stat[0], (ull)__popc(act_mask));
+        if (det_mask) atomicAdd(&p.stat[1], (ull)__popc(det_mask));
+        if (mc_mask) atomicAdd(&p.stat[3], (ull)__popc(mc_mask));
+    }
+    // appends
+    const ull mo = warp_append(p.n_mc, act == kActMC ? 1 : 0);
+    if (act == kActMC) {
+        if ((int64_t)mo < p.cap_mc) p.mc[mo] = me;
+        else atomicOr(p.flags, MBM_FLAG_OVERFLOW);
+    }
+    const ull bo = warp_append(p.n_base, act == kActBase ? 1 : 0);
+    if (act == kActBase) {
+        if ((int64_t)bo < p.cap_base) p.base[bo] = me;
+        else atomicOr(p.flags, MBM_FLAG_OVERFLOW);
+    }
+    const ull no = warp_append(p.n_next, n_kids);
+    for (int c = 0; c < n_kids; ++c) {
+        if ((int64_t)(no + c) < p.cap_next) p.next[no + c] = kids[c];
+        else atomicOr(p.flags, MBM_FLAG_OVERFLOW);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a7: Monte Carlo (Algorithms 3-5).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t r[4]) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    r[0] = c0;
+    r[1] = c1;
+    r[2] = c2;
+    r[3] = c3;
+}
+
+__device__ __forceinline__ int64_t draw_below(uint32_t r, int64_t n) {
+    return (int64_t)(((ull)r * (ull)n) >> 32);
+}
+
+// Distinct (u, w) from [b, b+n) minus x if excl; a uniform unordered pair.
+__device__ __forceinline__ void pair_from(int64_t b, int64_t n, bool excl, int64_t x, uint32_t r0,
+                                          uint32_t r1, int64_t& y, int64_t& z) {
+    const int64_t m = n - (excl ? 1 : 0);
+    int64_t u = draw_below(r0, m), w = draw_below(r1, m - 1);
+    if (w >= u) ++w;
+    if (excl) {
+        if (b + u >= x) ++u;
+        if (b + w >= x) ++w;
+    }
+    y = b + u;
+    z = b + w;
+}
+
+// One tuple containing sorted particle x (slot `slot`) of triple P.
+__device__ void draw_partners(const int64_t P[3], const int64_t bb[3], const int64_t nn[3], int slot,
+                              int64_t x, uint32_t r0, uint32_t r1, int64_t& y, int64_t& z) {
+    const bool e01 = P[0] == P[1], e12 = P[1] == P[2];
+    if (e01 && e12) {
+        pair_from(bb[0], nn[0], true, x, r0, r1, y, z);
+    } else if (e01) {
+        if (slot == 2) {
+            pair_from(bb[0], nn[0], false, x, r0, r1, y, z);
+        } else {
+            int64_t u = draw_below(r0, nn[0] - 1);
+            if (bb[0] + u >= x) ++u;
+            y = bb[0] + u;
+            z = bb[2] + draw_below(r1, nn[2]);
+        }
+    } else if (e12) {
+        if (slot == 0) {
+            pair_from(bb[1], nn[1], false, x, r0, r1, y, z);
+        } else {
+            y = bb[0] + draw_below(r0, nn[0]);
+            int64_t u = draw_below(r1, nn[1] - 1);
+            if (bb[1] + u >= x) ++u;
+            z = bb[1] + u;
+        }
+    } else {
+        const int o1 = slot == 0 ? 1 : 0, o2 = slot == 2 ? 1 : 2;
+        y = bb[o1] + draw_below(r0, nn[o1]);
+        z = bb[o2] + draw_below(r1, nn[o2]);
+    }
+}
+
+// phi of one point triple in FP32 bulk (direction-cosine form).
+__device__ __forceinline__ float phi_fp32(const float4* xh, const float4* xl, int64_t a, int64_t b,
+                                          int64_t c) {
+    float s;
+    const float4 ah = xh[a], al = xl[a], bh = xh[b], bl = xl[b], ch = xh[c], cl = xl[c];
+    const mbm_tile::PairF ab = mbm_tile::pair_unit(ah, al, bh, bl, &s);
+    const mbm_tile::PairF ac = mbm_tile::pair_unit(ah, al, ch, cl, &s);
+    const mbm_tile::PairF bc = mbm_tile::pair_unit(bh, bl, ch, cl, &s);
+    const float p1 = ab.ex * ac.ex + ab.ey * ac.ey + ab.ez * ac.ez;
+    const float p2 = ab.ex * bc.ex + ab.ey * bc.ey + ab.ez * bc.ez;
+    const float p3 = ac.ex * bc.ex + ac.ey * bc.ey + ac.ez * bc.ez;
+    const float n = fmaf(p1 * p2 * p3, -3.0f, 1.0f);
+    return n * (ab.rho * ac.rho * bc.rho);
+}
+
+// Particles of a candidate in order: slot 0's node, then each later distinct node.
+__device__ __forceinline__ void candidate_point(const Trav& p, const int64_t P[3], int64_t u,
+                                                int& slot, int64_t& x) {
+    int64_t off = 0;
+    for (int s = 0; s < 3; ++s) {
+        if (s > 0 && P[s] == P[s - 1]) continue;
+        int64_t b, e;
+        node_range(P[s], p.N, b, e);
+        if (u < off + (e - b)) {
+            slot = s;
+            x = b + (u - off);
+            return;
+        }
+        off += e - b;
+    }
+    slot = 2;
+    x = 0;
+}
+
+__global__ void mc_sizes_kernel(const int4* __restrict__ mc, int64_t n_mc, int64_t N,
+                                int64_t* chunks) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n_mc) return;
+    const int4 t = mc[c];
+    const int64_t P[3] = {t.x, t.y, t.z};
+    int64_t U = 0;
+    for (int s = 0; s < 3; ++s) {
+        if (s > 0 && P[s] == P[s - 1]) continue;
+        int64_t b, e;
+        node_range(P[s], N, b, e);
+        U += e - b;
+    }
+    chunks[c] = (U + 31) / 32;
+}
+
+// One warp per 32-particle chunk of a candidate (Algorithm 4 per particle).
+__global__ void mc_kernel(const int4* __restrict__ mc, int64_t c0, int64_t n_c,
+                          const int64_t* __restrict__ chunk_off /* exclusive, n_c + 1 */,
+                          int* cand_fail, double* est, Trav p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t rel = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (rel >= chunk_off[n_c] - chunk_off[0]) return;
+    const int64_t chunk = chunk_off[0] + rel;
+    int64_t lo = 0, hi = n_c;  // largest c with chunk_off[c] <= chunk
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) / 2;
+        if (chunk_off[mid] <= chunk) lo = mid;
+        else hi = mid;
+    }
+    const int64_t c = lo;
+    volatile int* fail = cand_fail + c;
+    if (*fail) return;  // warp-uniform
+    const int4 t = mc[c0 + c];
+    const int64_t P[3] = {t.x, t.y, t.z};
+    double n[3], T[3];
+    bool first[3];
+    triple_counts(p, P, n, T, first);
+    int64_t bb[3], nn[3];
+    int64_t U = 0;
+    for (int s = 0; s < 3; ++s) {
+        int64_t e;
+        node_range(P[s], p.N, bb[s], e);
+        nn[s] = e - bb[s];
+        if (first[s]) U += nn[s];
+    }
+    const int64_t u = (chunk - chunk_off[c]) * 32 + lane;
+    const bool active = u < U;
+    int slot = 0;
+    int64_t x = 0;
+    if (active) candidate_point(p, P, u, slot, x);
+    const double Ti = T[slot];
+    const double phil = p.nphil[P[slot]];
+    double mean = 0.0, m2 = 0.0;
+    int m = 0;
+    bool pass = false, done = !active;
+    int samples = 0, iter = 0;
+    while (__any_sync(0xffffffffu, !done)) {
+        if (!done) {
+            const uint32_t ctr1 = (uint32_t)P[0] | ((uint32_t)(m & 0xFF) << 24);
+            const uint32_t ctr2 = (uint32_t)P[1] | ((uint32_t)((m >> 8) & 0xFF) << 24);
+            uint32_t r[4];
+            philox4x32_10((uint32_t)x, ctr1, ctr2, (uint32_t)P[2], p.key0, p.key1, r);
+            int64_t y, zz;
+            draw_partners(P, bb, nn, slot, x, r[0], r[1], y, zz);
+            const double f = (double)phi_fp32(p.xh, p.xl, x, y, zz);
+            ++m;
+            ++samples;
+            const double dlt = __dsub_rn(f, mean);
+            mean = __dadd_rn(mean, __ddiv_rn(dlt, (double)m));
+            m2 = __dadd_rn(m2, __dmul_rn(dlt, __dsub_rn(f, mean)));
+            if (m >= 2) {
+                const double sig =
+                    __ddiv_rn(__dsqrt_rn(__ddiv_rn(m2, (double)(m - 1))), __dsqrt_rn((double)m));
+                const double lhs = __dmul_rn(p.z, sig);
+                double lb = __dsub_rn(phil, __dmul_rn(Ti, __dadd_rn(fabs(mean), __dmul_rn(p.z, sig))));
+                if (lb < 0.0) lb = 0.0;
+                const double rhs =
+                    p.mc_rule == 1
+                        ? __ddiv_rn(__dadd_rn(__ddiv_rn(__dmul_rn(p.eps, lb), Ti), p.tau), p.troot)
+                        : __ddiv_rn(__dadd_rn(__dmul_rn(p.eps, lb), p.tau), p.troot);
+                pass = lhs <= rhs;
+                if ((pass && m >= 30) || m >= p.m_limit) done = true;
+            } else if (m >= p.m_limit) {
+                pass = false;
+                done = true;
+            }
+            if (done && !pass) *fail = 1;
+        }
+        if ((++iter & 31) == 0) {  // another particle already failed: stop the warp
+            int f = lane == 0 ? *fail : 0;
+            if (__shfl_sync(0xffffffffu, f, 0)) break;
+        }
+    }
+    if (active) est[rel * 32 + lane] = __dmul_rn(Ti, mean);
+    int tot = samples;
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0 && tot) atomicAdd(&p.stat[5], (ull)tot);
+}
+
+// Algorithm 5 for passing candidates; failing ones go on to base/split.
+__global__ void mc_commit_kernel(const int4* __restrict__ mc, int64_t c0, int64_t n_c,
+                                 const int64_t* __restrict__ chunk_off, const int* cand_fail,
+                                 const double* est, Trav p) {
+    const int64_t c = blockIdx.x;
+    if (c >= n_c) return;
+    const int4 t = mc[c0 + c];
+    const int64_t P[3] = {t.x, t.y, t.z};
+    if (!cand_fail[c]) {
+        double n[3], T[3];
+        bool first[3];
+        triple_counts(p, P, n, T, first);
+        int64_t U = 0;
+        for (int s = 0; s < 3; ++s)
+            if (first[s]) U += (int64_t)n[s];
+        for (int64_t u = threadIdx.x; u < U; u += blockDim.x) {
+            int slot;
+            int64_t x;
+            candidate_point(p, P, u, slot, x);
+            atomicAdd(&p.pt_acc[x], est[chunk_off[c] * 32 + u - chunk_off[0] * 32]);
+            if (p.pt_cnt) atomicAdd(&p.pt_cnt[x], (ull)T[slot]);
+        }
+        if (threadIdx.x == 0) atomicAdd(&p.stat[2], 1ULL);
+        return;
+    }
+    if (threadIdx.x != 0) return;
+    if (is_leaf(p, P[0]) && is_leaf(p, P[1]) && is_leaf(p, P[2])) {
+        const ull o = atomicAdd(p.n_base, 1ULL);
+        if ((int64_t)o < p.cap_base) p.base[o] = t;
+        else atomicOr(p.flags, MBM_FLAG_OVERFLOW);
+        return;
+    }
+    int4 kids[4];
+    const int k = split_children(p, P, kids);
+    const ull o = atomicAdd(p.n_next, (ull)k);
+    for (int q = 0; q < k; ++q) {
+        if ((int64_t)(o + q) < p.cap_next) p.next[o + q] = kids[q];
+        else atomicOr(p.flags, MBM_FLAG_OVERFLOW);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// a9: top-down push and output in the caller's order.
+// ---------------------------------------------------------------------------
+__global__ void finalize_kernel(int64_t N, int depth, int64_t n_nodes, int64_t n_leaves,
+                                const int64_t* __restrict__ perm, const double* __restrict__ pt_acc,
+                                const double* __restrict__ node_acc, const ull* pt_cnt,
+                                const ull* node_cnt, double* out, int64_t* counts_out) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    int64_t q = (s << depth) / N;
+    const int64_t first_leaf = n_nodes - n_leaves;
+    int64_t b, e;
+    node_range(first_leaf + q, N, b, e);
+    while (b > s) {
+        --q;
+        node_range(first_leaf + q, N, b, e);
+    }
+    while (e <= s) {
+        ++q;
+        node_range(first_leaf + q, N, b, e);
+    }
+    int64_t v = first_leaf + q;
+    double acc = 0.0;
+    ull cnt = 0;
+    for (;;) {
+        acc += node_acc[v];
+        if (node_cnt) cnt += node_cnt[v];
+        if (v == 0) break;
+        v = (v - 1) / 2;
+    }
+    out[perm[s]] = pt_acc[s] + acc;
+    if (counts_out) counts_out[perm[s]] = (int64_t)(cnt + pt_cnt[s]);
+}
+
+// Two-sided normal quantile: z with P(|Z| > z) = alpha, bisection on erfc.
+double z_two_sided(double alpha) {
+    if (!(alpha > 0.0)) return INFINITY;
+    double lo = 0.0, hi = 40.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (std::erfc(mid / std::sqrt(2.0)) > alpha) lo = mid;
+        else hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+unsigned grid_of(int64_t threads, int block) {
+    int64_t g = (threads + block - 1) / block;
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, 2147483647));
+}
+
+// (I,J,K) chunk triples, I <= J <= K < c.
+std::vector<int4> chunk_combos(int c) {
+    std::vector<int4> v;
+    for (int i = 0; i < c; ++i)
+        for (int j = i; j < c; ++j)
+            for (int k = j; k < c; ++k) v.push_back(make_int4(i, j, k, 0));
+    return v;
+}
+
+struct Carve {
+    char* p;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t n) {
+        off = mbm_align_up(off, 256);
+        T* r = reinterpret_cast<T*>(p + off);
+        off += n * sizeof(T);
+        return r;
+    }
+};
+
+size_t carve_size(const std::vector<size_t>& parts) {
+    size_t s = 0;
+    for (size_t b : parts) s = mbm_align_up(s, 256) + b;
+    return mbm_align_up(s, 256);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Tree build (ABI).
+// ---------------------------------------------------------------------------
+static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm_config& cfg,
+                             cudaStream_t s, mbm_tree** out) {
+    if (N < 3) return mbm_fail(MBM_EINVAL, "tree needs N >= 3");
+    if (cfg.leaf_size < 2 || cfg.leaf_size > kTile) return mbm_fail(MBM_EINVAL, "leaf_size must be in [2, 32]");
+    if (cfg.seed_levels < 0 || cfg.seed_levels > 4) return mbm_fail(MBM_EINVAL, "seed_levels must be in [0, 4]");
+    const int depth = tree_depth(N, cfg.leaf_size);
+    const int64_t n_nodes = ((int64_t)2 << depth) - 1, n_leaves = (int64_t)1 << depth;
+    if (n_nodes >= (1 << 24)) return mbm_fail(MBM_EINVAL, "tree too large (node ids are 24-bit)");
+    mbm_tree* t = new (std::nothrow) mbm_tree();
+    if (!t) return mbm_fail(MBM_ENOMEM, "host allocation failed");
+    t->ctx = ctx;
+    t->device = ctx->device;
+    t->N = N;
+    t->leaf_size = cfg.leaf_size;
+    t->depth = depth;
+    t->n_nodes = n_nodes;
+    t->n_leaves = n_leaves;
+    t->seed_levels = cfg.seed_levels;
+    const std::vector<size_t> parts = {
+        (size_t)N * 8, (size_t)N * 24, (size_t)N * 16, (size_t)N * 16,  // perm xs xh xl
+        (size_t)n_nodes * 24, (size_t)n_nodes * 24, (size_t)n_nodes * 24,  // lo hi cen
+        (size_t)n_nodes * 8, (size_t)n_nodes * 8};                          // diam2 phil
+    t->bytes = carve_size(parts);
+    mbm_status st = mbm_budget_charge(ctx, t->bytes);
+    if (st != MBM_OK) {
+        delete t;
+        return st;
+    }
+    cudaError_t e = cudaMalloc(&t->mem, t->bytes);
+    if (e != cudaSuccess) {
+        mbm_budget_release(ctx, t->bytes);
+        delete t;
+        return mbm_cuda_fail(e, "cudaMalloc(tree)");
+    }
+    Carve cv{static_cast<char*>(t->mem)};
+    t->perm = cv.take<int64_t>(N);
+    t->xs = cv.take<double>(3 * N);
+    t->xh = cv.take<float4>(N);
+    t->xl = cv.take<float4>(N);
+    t->nlo = cv.take<double>(3 * n_nodes);
+    t->nhi = cv.take<double>(3 * n_nodes);
+    t->ncen = cv.take<double>(3 * n_nodes);
+    t->ndiam2 = cv.take<double>(n_nodes);
+    t->nphil = cv.take<double>(n_nodes);
+
+    // Temporary scratch: box partials, keys/indices (double-buffered), CUB temp, seed sums.
+    const int nb = 256;
+    size_t cub_bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, cub_bytes, (uint64_t*)nullptr, (uint64_t*)nullptr,
+                                    (int*)nullptr, (int*)nullptr, (int)N, 0, 63, s);
+    const int sd = std::max(0, depth - cfg.seed_levels);
+    const std::vector<size_t> sparts = {(size_t)nb * 48, 64, (size_t)N * 8, (size_t)N * 8,
+                                        (size_t)N * 4, (size_t)N * 4, cub_bytes, (size_t)N * 8,
+                                        1024 * 16};
+    st = mbm_scratch_reserve(ctx, carve_size(sparts));
+    if (st != MBM_OK) {
+        mbm_tree_free(t);
+        return st;
+    }
+    Carve sc{static_cast<char*>(ctx->scratch)};
+    double* part = sc.take<double>(nb * 6);
+    double* box = sc.take<double>(8);
+    uint64_t* k0 = sc.take<uint64_t>(N);
+    uint64_t* k1 = sc.take<uint64_t>(N);
+    int* i0 = sc.take<int>(N);
+    int* i1 = sc.take<int>(N);
+    void* cub_tmp = sc.take<char>(cub_bytes);
+    double* seed = sc.take<double>(N);
+    int4* combos = sc.take<int4>(1024);
+
+#define TRY_LAUNCH()                                                           \
+    do {                                                                       \
+        cudaError_t e_ = cudaGetLastError();                                   \
+        if (e_ != cudaSuccess) {                                               \
+            mbm_tree_free(t);                                                  \
+            return mbm_cuda_fail(e_, "tree build launch");                     \
+        }                                                                      \
+    } while (0)
+
+    bbox_partial_kernel<<<nb, 256, 0, s>>>(X, N, part);
+    bbox_final_kernel<<<1, 32, 0, s>>>(part, nb, box);
+    morton_kernel<<<grid_of(N, 256), 256, 0, s>>>(X, N, box, k0, i0, ctx->d_flags);
+    TRY_LAUNCH();
+    e = cub::DeviceRadixSort::SortPairs(cub_tmp, cub_bytes, k0, k1, i0, i1, (int)N, 0, 63, s);
+    if (e != cudaSuccess) {
+        mbm_tree_free(t);
+        return mbm_cuda_fail(e, "radix sort");
+    }
+    gather_kernel<<<grid_of(N, 256), 256, 0, s>>>(X, N, i1, t->perm, t->xs, t->xh, t->xl);
+    const int64_t first_leaf = n_nodes - n_leaves;
+    leaf_stats_kernel<<<grid_of(n_leaves * 32, 256), 256, 0, s>>>(t->xs, N, first_leaf, n_leaves,
+                                                                  t->nlo, t->nhi, t->ncen);
+    for (int d = depth - 1; d >= 0; --d) {
+        const int64_t first = ((int64_t)1 << d) - 1, cnt = (int64_t)1 << d;
+        internal_stats_kernel<<<grid_of(cnt, 256), 256, 0, s>>>(first, cnt, t->nlo, t->nhi,
+                                                                t->ncen);
+    }
+    node_finish_kernel<<<grid_of(n_nodes, 256), 256, 0, s>>>(N, n_nodes, t->nlo, t->nhi, t->ncen,
+                                                             t->ndiam2);
+    TRY_LAUNCH();
+
+    // Phi^l seed: exact sums over triples inside each seed node.
+    const int64_t max_seed = (N + ((int64_t)1 << sd) - 1) >> sd;  // ceil(N / 2^sd)
+    const int chunks = (int)((max_seed + kTile - 1) / kTile);
+    std::vector<int4> cmb = chunk_combos(chunks);
+    if (cmb.size() > 1024) {
+        mbm_tree_free(t);
+        return mbm_fail(MBM_EINVAL, "seed node too large");
+    }
+    e = cudaMemcpyAsync(combos, cmb.data(), cmb.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(seed, 0, (size_t)N * 8, s);
+    if (e != cudaSuccess) {
+        mbm_tree_free(t);
+        return mbm_cuda_fail(e, "seed set-up");
+    }
+    const int64_t n_seed_nodes = (int64_t)1 << sd;
+    const size_t wsm = sizeof(WarpSmem) * kRangeWarps;
+    cudaFuncSetAttribute((const void*)seed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)wsm);
+    seed_kernel<<<grid_of(n_seed_nodes * (int64_t)cmb.size() * 32, kRangeWarps * 32),
+                  kRangeWarps * 32, wsm, s>>>(t->xh, t->xl, N, sd, n_seed_nodes, combos,
+                                              (int)cmb.size(), seed, ctx->d_flags);
+    phil_leaf_kernel<<<grid_of(n_leaves * 32, 256), 256, 0, s>>>(seed, N, first_leaf, n_leaves,
+                                                                 t->nphil);
+    for (int d = depth - 1; d >= 0; --d) {
+        const int64_t first = ((int64_t)1 << d) - 1, cnt = (int64_t)1 << d;
+        phil_internal_kernel<<<grid_of(cnt, 256), 256, 0, s>>>(first, cnt, t->nphil);
+    }
+    TRY_LAUNCH();
+#undef TRY_LAUNCH
+    *out = t;
+    return MBM_OK;
+}
+
+extern "C" mbm_status mbm_tree_build(mbm_ctx* ctx, const double* X_dev, int64_t N,
+                                     const mbm_config* cfg, mbm_stream_t stream, mbm_tree** out) {
+    if (!ctx || !out) return mbm_fail(MBM_EINVAL, "NULL ctx or out");
+    if (!X_dev) return mbm_fail(MBM_EINVAL, "NULL X");
+    *out = nullptr;
+    mbm_config c;
+    if (cfg) c = *cfg;
+    else mbm_config_default(&c);
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    MBM_CUDA_TRY(cudaSetDevice(ctx->device));
+    return build_tree(ctx, X_dev, N, c, reinterpret_cast<cudaStream_t>(stream), out);
+}
+
+extern "C" mbm_status mbm_tree_free(mbm_tree* t) {
+    if (!t) return MBM_OK;
+    cudaSetDevice(t->device);
+    cudaDeviceSynchronize();
+    if (t->mem) cudaFree(t->mem);
+    if (t->ctx) mbm_budget_release(t->ctx, t->bytes);
+    delete t;
+    return MBM_OK;
+}
+
+extern "C" mbm_status mbm_tree_info(const mbm_tree* t, int64_t* n_nodes, int64_t* n_leaves,
+                                    int32_t* depth) {
+    if (!t) return mbm_fail(MBM_EINVAL, "NULL tree");
+    if (n_nodes) *n_nodes = t->n_nodes;
+    if (n_leaves) *n_leaves = t->n_leaves;
+    if (depth) *depth = t->depth;
+    return MBM_OK;
+}
+
+extern "C" mbm_status mbm_tree_export(const mbm_tree* t, int64_t* perm, double* lo, double* hi,
+                                      double* cen, double* phil, mbm_stream_t stream) {
+    if (!t) return mbm_fail(MBM_EINVAL, "NULL tree");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const auto d2d = cudaMemcpyDeviceToDevice;
+    if (perm) MBM_CUDA_TRY(cudaMemcpyAsync(perm, t->perm, (size_t)t->N * 8, d2d, s));
+    if (lo) MBM_CUDA_TRY(cudaMemcpyAsync(lo, t->nlo, (size_t)t->n_nodes * 24, d2d, s));
+    if (hi) MBM_CUDA_TRY(cudaMemcpyAsync(hi, t->nhi, (size_t)t->n_nodes * 24, d2d, s));
+    if (cen) MBM_CUDA_TRY(cudaMemcpyAsync(cen, t->ncen, (size_t)t->n_nodes * 24, d2d, s));
+    if (phil) MBM_CUDA_TRY(cudaMemcpyAsync(phil, t->nphil, (size_t)t->n_nodes * 8, d2d, s));
+    return MBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tree potential.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Timer {
+    bool on;
+    cudaEvent_t e[6];
+    cudaStream_t s;
+    Timer(bool on_, cudaStream_t s_) : on(on_), s(s_) {
+        if (on)
+            for (auto& x : e) cudaEventCreate(&x);
+    }
+    ~Timer() {
+        if (on)
+            for (auto& x : e) cudaEventDestroy(x);
+    }
+    void mark(int i) {
+        if (on) cudaEventRecord(e[i], s);
+    }
+    double ms(int a, int b) {
+        float v = 0.f;
+        if (on) cudaEventElapsedTime(&v, e[a], e[b]);
+        return v;
+    }
+};
+
+}  // namespace
+
+mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double eps, double alpha,
+                              bool absolute, const mbm_config& cfg, mbm_tree* tree_in, double* phi,
+                              mbm_stats* stats, cudaStream_t s) {
+    if (cfg.m_limit < 2 || cfg.m_limit > 65535) return mbm_fail(MBM_EINVAL, "m_limit must be in [2, 65535]");
+    if (!(cfg.zeta >= 0.0)) return mbm_fail(MBM_EINVAL, "zeta must be >= 0");
+    if (!(cfg.tau >= 0.0)) return mbm_fail(MBM_EINVAL, "tau must be >= 0");
+    Timer tm(stats != nullptr || ctx->timing, s);
+    tm.mark(0);
+    mbm_tree* tree = tree_in;
+    bool own = false;
+    if (tree) {
+        if (tree->N != N || tree->device != ctx->device)
+            return mbm_fail(MBM_EINVAL, "tree does not match X");
+    } else {
+        MBM_TRY(build_tree(ctx, X, N, cfg, s, &tree));
+        own = true;
+    }
+    tm.mark(1);
+    struct Owner {
+        mbm_tree* t;
+        bool own;
+        ~Owner() {
+            if (own) mbm_tree_free(t);
+        }
+    } owner{tree, own};
+
+    const int64_t n_nodes = tree->n_nodes, n_leaves = tree->n_leaves;
+    const bool counting = cfg.tuple_counts != nullptr;
+    int64_t cap_front = std::max<int64_t>(1 << 16, 4 * N), cap_mc = std::max<int64_t>(1 << 14, N / 4);
+    int64_t cap_base = std::max<int64_t>(1 << 18, 8 * N), cap_est = std::max<int64_t>(1 << 20, 8 * N);
+    const double z = z_two_sided(alpha);
+
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        const std::vector<size_t> parts = {
+            (size_t)N * 8,           (size_t)n_nodes * 8,                    // pt_acc node_acc
+            counting ? (size_t)N * 8 : 0, counting ? (size_t)n_nodes * 8 : 0,  // counts
+            (size_t)cap_front * 16,  (size_t)cap_front * 16,                 // front next
+            (size_t)cap_mc * 16,     (size_t)cap_base * 16,                  // mc base
+            (size_t)cap_mc * 8 + 16, (size_t)cap_mc * 4,                     // chunk_off fail
+            (size_t)cap_est * 8,     256,                                    // est, counters
+            4096};
+        size_t cub_bytes = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, cub_bytes, (int64_t*)nullptr, (int64_t*)nullptr,
+                                      (int)(cap_mc + 1), s);
+        std::vector<size_t> all = parts;
+        all.push_back(cub_bytes);
+        MBM_TRY(mbm_scratch_reserve(ctx, carve_size(all)));
+        Carve sc{static_cast<char*>(ctx->scratch)};
+        double* pt_acc = sc.take<double>(N);
+        double* node_acc = sc.take<double>(n_nodes);
+        ull* pt_cnt = counting ? sc.take<ull>(N) : nullptr;
+        ull* node_cnt = counting ? sc.take<ull>(n_nodes) : nullptr;
+        int4* front = sc.take<int4>(cap_front);
+        int4* next = sc.take<int4>(cap_front);
+        int4* mcl = sc.take<int4>(cap_mc);
+        int4* basel = sc.take<int4>(cap_base);
+        int64_t* chunk_off = sc.take<int64_t>(cap_mc + 2);
+        int* cand_fail = sc.take<int>(cap_mc);
+        double* est = sc.take<double>(cap_est);
+        ull* ctr = sc.take<ull>(32);  // 0 n_next 1 n_mc 2 n_base 3.. stats
+        sc.take<char>(4096);
+        void* cub_tmp = sc.take<char>(cub_bytes);
+        ull* h = reinterpret_cast<ull*>(ctx->h_flags) + 8;  // pinned, after the status word
+
+        MBM_CUDA_TRY(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+        MBM_CUDA_TRY(cudaMemsetAsync(pt_acc, 0, (size_t)N * 8, s));
+        MBM_CUDA_TRY(cudaMemsetAsync(node_acc, 0, (size_t)n_nodes * 8, s));
+        if (counting) {
+            MBM_CUDA_TRY(cudaMemsetAsync(pt_cnt, 0, (size_t)N * 8, s));
+            MBM_CUDA_TRY(cudaMemsetAsync(node_cnt, 0, (size_t)n_nodes * 8, s));
+        }
+        MBM_CUDA_TRY(cudaMemsetAsync(ctr, 0, 32 * sizeof(ull), s));
+        const int4 root = make_int4(0, 0, 0, 0);
+        MBM_CUDA_TRY(cudaMemcpyAsync(front, &root, sizeof(int4), cudaMemcpyHostToDevice, s));
+
+        Trav p;
+        p.N = N;
+        p.n_nodes = n_nodes;
+        p.n_leaves = n_leaves;
+        p.nlo = tree->nlo;
+        p.nhi = tree->nhi;
+        p.ncen = tree->ncen;
+        p.ndiam2 = tree->ndiam2;
+        p.nphil = tree->nphil;
+        p.xs = tree->xs;
+        p.xh = tree->xh;
+        p.xl = tree->xl;
+        p.eps = absolute ? 0.0 : eps;
+        p.tau = absolute ? eps : cfg.tau;
+        p.troot = (double)(N - 1) * (double)(N - 2) * 0.5;
+        p.zeta = cfg.zeta;
+        p.z = z;
+        p.alpha = alpha;
+        p.m_limit = cfg.m_limit;
+        p.mc_rule = cfg.mc_rule;
+        p.key0 = (uint32_t)cfg.seed;
+        p.key1 = (uint32_t)(cfg.seed >> 32);
+        p.node_acc = node_acc;
+        p.pt_acc = pt_acc;
+        p.node_cnt = node_cnt;
+        p.pt_cnt = pt_cnt;
+        p.n_next = ctr + 0;
+        p.n_mc = ctr + 1;
+        p.n_base = ctr + 2;
+        p.stat = ctr + 3;
+        p.cap_next = cap_front;
+        p.cap_mc = cap_mc;
+        p.cap_base = cap_base;
+        p.mc = mcl;
+        p.base = basel;
+        p.flags = ctx->d_flags;
+
+        tm.mark(2);
+        int64_t n_front = 1, levels = 0;
+        bool overflow = false;
+        while (n_front > 0) {
+            ++levels;
+            MBM_CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(ull), s));  // n_next, n_mc
+            p.next = next;
+            classify_kernel<<<grid_of(n_front, 256), 256, 0, s>>>(front, n_front, p);
+            MBM_CUDA_TRY(cudaGetLastError());
+            MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 3 * sizeof(ull), cudaMemcpyDeviceToHost, s));
+            MBM_CUDA_TRY(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+            MBM_CUDA_TRY(cudaStreamSynchronize(s));
+            if (ctx->h_flags[0] & MBM_FLAG_OVERFLOW) {
+                overflow = true;
+                break;
+            }
+            const int64_t n_mc = (int64_t)h[1];
+            if (n_mc > 0) {
+                // chunk offsets, then candidates in batches that fit the estimate buffer
+                mc_sizes_kernel<<<grid_of(n_mc, 256), 256, 0, s>>>(mcl, n_mc, N, chunk_off);
+                MBM_CUDA_TRY(cudaMemsetAsync(chunk_off + n_mc, 0, sizeof(int64_t), s));
+                MBM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(cub_tmp, cub_bytes, chunk_off, chunk_off,
+                                                           (int)(n_mc + 1), s));
+                std::vector<int64_t> off(n_mc + 1);
+                MBM_CUDA_TRY(cudaMemcpyAsync(off.data(), chunk_off, (n_mc + 1) * sizeof(int64_t),
+                                             cudaMemcpyDeviceToHost, s));
+                MBM_CUDA_TRY(cudaStreamSynchronize(s));
+                MBM_CUDA_TRY(cudaMemsetAsync(cand_fail, 0, (size_t)n_mc * sizeof(int), s));
+                int64_t c0 = 0;
+                while (c0 < n_mc) {
+                    int64_t c1 = c0 + 1;
+                    while (c1 < n_mc && (off[c1 + 1] - off[c0]) * 32 <= cap_est) ++c1;
+                    if ((off[c1] - off[c0]) * 32 > cap_est) {  // one candidate too large
+                        overflow = true;
+                        break;
+                    }
+                    const int64_t chunks = off[c1] - off[c0];
+                    mc_kernel<<<grid_of(chunks * 32, 256), 256, 0, s>>>(
+                        mcl + c0, 0, c1 - c0, chunk_off + c0, cand_fail + c0, est, p);
+                    mc_commit_kernel<<<(unsigned)(c1 - c0), 256, 0, s>>>(
+                        mcl + c0, 0, c1 - c0, chunk_off + c0, cand_fail + c0, est, p);
+                    MBM_CUDA_TRY(cudaGetLastError());
+                    c0 = c1;
+                }
+                if (overflow) break;
+                MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 3 * sizeof(ull), cudaMemcpyDeviceToHost, s));
+                MBM_CUDA_TRY(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+                MBM_CUDA_TRY(cudaStreamSynchronize(s));
+                if (ctx->h_flags[0] & MBM_FLAG_OVERFLOW) {
+                    overflow = true;
+                    break;
+                }
+            }
+            n_front = (int64_t)h[0];
+            std::swap(front, next);
+        }
+        if (overflow) {
+            MBM_CUDA_TRY(cudaStreamSynchronize(s));
+            cap_front *= 2;
+            cap_mc *= 2;
+            cap_base *= 2;
+            cap_est *= 2;
+            continue;
+        }
+        tm.mark(3);
+        const int64_t n_base = (int64_t)h[2];
+        if (n_base > 0) {
+            const size_t wsm = sizeof(WarpSmem) * kRangeWarps;
+            cudaFuncSetAttribute((const void*)base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)wsm);
+            mbm_time_begin(ctx, s);
+            base_kernel<<<grid_of(n_base * 32, kRangeWarps * 32), kRangeWarps * 32, wsm, s>>>(
+                tree->xh, tree->xl, N, basel, n_base, pt_acc, ctx->d_flags);
+            mbm_time_end(ctx, s);
+            MBM_CUDA_TRY(cudaGetLastError());
+            if (counting)
+                base_count_kernel<<<grid_of(n_base * 32, 256), 256, 0, s>>>(N, basel, n_base, pt_cnt);
+        }
+        tm.mark(4);
+        finalize_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, tree->depth, n_nodes, n_leaves, tree->perm,
+                                                        pt_acc, node_acc, pt_cnt, node_cnt, phi,
+                                                        cfg.tuple_counts);
+        MBM_CUDA_TRY(cudaGetLastError());
+        tm.mark(5);
+        if (stats) {
+            ull st[9];
+            MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 9 * sizeof(ull), cudaMemcpyDeviceToHost, s));
+            MBM_CUDA_TRY(cudaStreamSynchronize(s));
+            std::memcpy(st, h, sizeof(st));
+            stats->node_triples_visited = (int64_t)st[3];
+            stats->det_prunes = (int64_t)st[4];
+            stats->mc_prunes = (int64_t)st[5];
+            stats->mc_attempts = (int64_t)st[6];
+            stats->base_cases = (int64_t)st[2];
+            stats->mc_samples = (int64_t)st[8];
+            stats->levels = levels;
+            stats->ms_build = tm.ms(0, 1);
+            stats->ms_traverse = tm.ms(2, 3);
+            stats->ms_base = tm.ms(3, 4);
+            stats->ms_finalize = tm.ms(4, 5);
+        }
+        if (cfg.validate) return mbm_check_flags(ctx, s);
+        return MBM_OK;
+    }
+    return mbm_fail(MBM_EOVERFLOW, "traversal work lists overflowed after retries");
 }

@@ -1,0 +1,150 @@
+"""GPU multi-tree path (steps a4-a9) against the oracle.
+
+What is unique is checked exactly; what may legitimately differ is checked
+for validity:
+  * the tree (permutation, boxes) equals the oracle's definition exactly;
+  * eps = tau = 0 admits no prune: the result is the exact sum (FP32 bar:
+    |error| <= 3e-6 sum_t |phi_t|, the exhaustive FP32-bulk bar);
+  * per-particle tuple counts of all prunes and base cases equal C(N-1, 2)
+    exactly (integer invariant of the partition, Fig. 4);
+  * deterministic rule: the same prunes as the serial restatement (Phi^l is
+    fixed before the traversal, so the breadth-first GPU order decides as the
+    depth-first recursion does), results equal to the FP32 bar, and the
+    guarantee of Sec. 5 (every particle within eps |Phi| + tau);
+  * Monte Carlo rule: the same Philox draws as the restatement; sample phi is
+    FP32 on the GPU and FP64 in the oracle, so a stop test within rounding of
+    its threshold may go the other way: at least 99 % of particles agree to
+    the FP32 bar, prune counts agree to 2 %, and the probabilistic guarantee
+    (>= 1 - alpha within eps, binomial slack) holds on both.
+"""
+from math import comb
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import tree as otree
+from paper_1105_2769_gb300 import _lib, api, inputs
+
+pytestmark = pytest.mark.gpu
+
+FP32_BAR = 3e-6
+
+
+@pytest.fixture(scope="module")
+def gmm():
+    X = inputs.gaussian_mixture(1200, 6, 10.0, 0.5, 1.5, 0.05, 5)
+    ex, ab = oracle.phi(X, with_abs=True)
+    return X, ex, ab
+
+
+def _gpu_tree(X, eps, alpha, mode="tree", **cfg):
+    Xd = torch.from_numpy(X).cuda()
+    counts = torch.zeros(len(X), dtype=torch.int64, device="cuda")
+    phi, st = api.potential(Xd, eps=eps, alpha=alpha, mode=mode, config=api.tree_config(**cfg),
+                            stats=True, tuple_counts=counts)
+    return phi.cpu().numpy(), counts.cpu().numpy(), st
+
+
+def test_tree_layout_matches_definition(gmm):
+    X, _, _ = gmm
+    t = api.Tree(torch.from_numpy(X).cuda())
+    got = t.export()
+    ref = otree.tree_layout(X, 32)
+    assert np.array_equal(got["perm"], ref["perm"])
+    assert np.array_equal(got["lo"], ref["lo"]) and np.array_equal(got["hi"], ref["hi"])
+    np.testing.assert_allclose(got["cen"], ref["cen"], rtol=1e-13, atol=1e-12)
+    # Phi^l seed: |exact sum over the seed node (2 levels above the leaves)|, min per node
+    d = ref["depth"]
+    sd = max(0, d - 2)
+    seed = np.zeros(len(X))
+    seed_abs = np.zeros(len(X))
+    for q in range(1 << sd):
+        v = (1 << sd) - 1 + q
+        b, e = ref["begin"][v], ref["end"][v]
+        s, a = oracle.phi(X[ref["perm"][b:e]], with_abs=True)
+        seed[b:e], seed_abs[b:e] = s, a
+    leaves = range((1 << d) - 1, (2 << d) - 1)
+    for v in leaves:
+        b, e = ref["begin"][v], ref["end"][v]
+        want = np.abs(seed[b:e]).min()
+        assert abs(got["phil"][v] - want) <= FP32_BAR * seed_abs[b:e].max()
+    t.close()
+
+
+def test_eps_zero_is_exact(gmm):
+    X, ex, ab = gmm
+    phi, cnt, st = _gpu_tree(X, 0.0, 0.0)
+    assert st["det_prunes"] == 0 and st["mc_prunes"] == 0
+    assert np.all(np.abs(phi - ex) <= FP32_BAR * ab)
+    assert np.all(cnt == comb(len(X) - 1, 2))
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.01])
+def test_deterministic_parity_and_guarantee(gmm, eps):
+    X, ex, ab = gmm
+    phi, cnt, st = _gpu_tree(X, eps, 0.0)
+    ref, rcnt, rst = otree.tree_potential(X, eps=eps, alpha=0.0, with_counts=True)
+    print(f"eps={eps}: gpu {st['det_prunes']} det prunes, oracle {rst['det_prunes']}")
+    assert np.all(cnt == comb(len(X) - 1, 2))
+    assert st["det_prunes"] == rst["det_prunes"] > 0
+    assert st["node_triples_visited"] == rst["visited"]
+    assert np.all(np.abs(phi - ref) <= FP32_BAR * ab)
+    assert np.all(np.abs(phi - ex) <= eps * np.abs(ex) + FP32_BAR * ab)
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.01])
+def test_monte_carlo_parity_and_guarantee(gmm, eps):
+    X, ex, ab = gmm
+    alpha = 0.05
+    phi, cnt, st = _gpu_tree(X, eps, alpha)
+    ref, rcnt, rst = otree.tree_potential(X, eps=eps, alpha=alpha, with_counts=True)
+    print(f"eps={eps}: gpu mc {st['mc_prunes']}/{st['mc_attempts']}, "
+          f"oracle mc {rst['mc_prunes']}/{rst['mc_attempts']}")
+    assert np.all(cnt == comb(len(X) - 1, 2))
+    assert st["mc_prunes"] > 0
+    assert abs(st["mc_prunes"] - rst["mc_prunes"]) <= max(2, 0.02 * rst["mc_prunes"])
+    agree = np.abs(phi - ref) <= FP32_BAR * ab
+    assert agree.mean() >= 0.99
+    n = len(X)
+    slack = 3.0 * np.sqrt(alpha * (1 - alpha) / n)
+    within = np.abs(phi - ex) <= eps * np.abs(ex)
+    assert within.mean() >= 1 - alpha - slack
+
+
+def test_absolute_rule(gmm):
+    X, ex, ab = gmm
+    tau = 1e-3 * float(np.median(np.abs(ex)))
+    phi, cnt, st = _gpu_tree(X, tau, 0.0, mode="tree_abs")
+    assert np.all(cnt == comb(len(X) - 1, 2))
+    assert st["det_prunes"] > 0
+    assert np.all(np.abs(phi - ex) <= tau + FP32_BAR * ab)
+
+
+def test_tree_reuse_and_small_inputs(gmm):
+    X, ex, ab = gmm
+    Xd = torch.from_numpy(X).cuda()
+    t = api.Tree(Xd)
+    a = api.potential(Xd, eps=0.1, mode="tree", tree=t).cpu().numpy()
+    b = api.potential(Xd, eps=0.1, mode="tree").cpu().numpy()
+    assert np.all(np.abs(a - b) <= 1e-9 * ab)
+    c = api.potential(Xd, eps=0.0, mode="tree", tree=t).cpu().numpy()
+    assert np.all(np.abs(c - ex) <= FP32_BAR * ab)
+    t.close()
+    for n in (3, 5, 40):
+        Xs = inputs.uniform_cube(n, 1.0, 0.05, 200 + n)
+        r = oracle.phi(Xs, with_abs=True)
+        g = api.potential(torch.from_numpy(Xs).cuda(), eps=0.05, alpha=0.05, mode="tree")
+        assert np.all(np.abs(g.cpu().numpy() - r[0]) <= 0.05 * np.abs(r[0]) + FP32_BAR * r[1])
+
+
+def test_bad_arguments(gmm):
+    X, _, _ = gmm
+    Xd = torch.from_numpy(X).cuda()
+    with pytest.raises(_lib.MbmError):
+        api.potential(Xd, eps=0.1, alpha=1.0, mode="tree")
+    with pytest.raises(_lib.MbmError):
+        api.potential(Xd, eps=-1.0, mode="tree")
+    with pytest.raises(_lib.MbmError):
+        api.potential(Xd, eps=0.1, mode="tree", config=api.tree_config(leaf_size=64))
