@@ -63,11 +63,11 @@ typedef struct {
     double tau;          /* absolute error term of Def. 2.3 (0 = pure relative) */
     int32_t leaf_size;   /* leaf threshold of Algorithm 1 (default 32, range 2..32) */
     int32_t m_limit;     /* Monte Carlo sample cap of Algorithm 4 (default 256, <= 65535) */
-    double zeta;         /* speed-up factor of Algorithm 3 (default 4) */
+    double zeta;         /* speed-up factor of Algorithm 3 (default 32) */
     uint64_t seed;       /* Philox-4x32-10 key for Monte Carlo draws */
     int32_t mc_rule;     /* 0 = relative stop test with T_i on both terms, 1 = as printed */
     int32_t validate;    /* 1: synchronise and report non-finite/coincident input */
-    int32_t seed_levels; /* Phi^l seed node = ancestor this many levels above a leaf (default 2) */
+    int32_t seed_levels; /* Phi^l seed node = ancestor this many levels above a leaf (default 3) */
     int32_t reserved0;
     int64_t* tuple_counts; /* optional device int64[N]: point triples credited to each
                               particle by prunes and base cases (validation; NULL = off) */
@@ -149,6 +149,20 @@ mbm_status mbm_potential_ex(mbm_ctx* ctx, const double* X_dev, int64_t N, double
 mbm_status mbm_potential_host(mbm_ctx* ctx, const double* X_host, int64_t N, double eps,
                               double alpha, int mode, const mbm_config* cfg,
                               double* phi_host, mbm_stream_t stream);
+
+/*
+ * Exact Phi (Eq. 1) of selected particles only, FP32 bulk with FP64
+ * accumulation: out_dev[q] = Phi(x_{idx_dev[q]}) over all pairs j < k of the
+ * whole set. Used as the reference for tree accuracy at sizes where the full
+ * exhaustive sum is out of reach (cost: n_idx * C(N-1, 2) triples).
+ *   idx_dev : n_idx int64 device indices in [0, N) (0 <= n_idx <= 2^20).
+ *   out_dev : n_idx FP64 device array, written.
+ * Indices are not range-checked on the device; out-of-range indices are
+ * the caller's error. Asynchronous on `stream`.
+ */
+mbm_status mbm_potential_sampled(mbm_ctx* ctx, const double* X_dev, int64_t N,
+                                 const int64_t* idx_dev, int64_t n_idx, double* out_dev,
+                                 mbm_stream_t stream);
 
 /*
  * Build the spatial tree of Sec. 3 (bottom-up phase) for X_dev (N x 3 FP64,

@@ -33,8 +33,8 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def tree_potential(X, eps=0.0, tau=0.0, alpha=0.0, leaf_size=32, m_limit=256, zeta=4.0,
-                   seed=0x5eed5eed, mc_rule=0, seed_up=2, with_counts=False):
+def tree_potential(X, eps=0.0, tau=0.0, alpha=0.0, leaf_size=32, m_limit=256, zeta=32.0,
+                   seed=0x5eed5eed, mc_rule=0, seed_up=3, with_counts=False):
     """Serial restatement of the multi-tree algorithm; returns (Phi, counts, stats)."""
     X = np.ascontiguousarray(X, dtype=np.float64)
     n = len(X)

@@ -14,7 +14,9 @@
  *            bound on |Phi|: seeded before the traversal with |S(x)|, S the
  *            exact sum over triples inside x's seed node (the ancestor
  *            seed_up levels above its leaf); Phi^l(P) = min over P's points
- *            (Sec. 5, Phi^l(P) = min over children). The paper's Phi^l +
+ *            (Sec. 5, Phi^l(P) = min over children). The Monte Carlo stop
+ *            test runs per particle and uses the particle's own Phi^l(x)
+ *            (Algorithm 5 keeps Phi^l per particle). The paper's Phi^l +
  *            delta^l (Eq. deterministic_prune) becomes Phi^l - T_i max|phi|,
  *            and Phi^l + T_i (mu - z sigma) (Eq. prob_rel_error_termination)
  *            becomes Phi^l - T_i (|mu| + z sigma): the magnitude left after
@@ -79,6 +81,7 @@ typedef struct {
     double* cen;       /* centre of mass, 3 per node */
     double* diam2;     /* squared bbox diagonal */
     double* phil;      /* Phi^l per node */
+    double* pphil;     /* Phi^l per sorted point, |S(x)| */
 } otree;
 
 static uint64_t spread3(uint32_t v) {
@@ -173,7 +176,7 @@ static void tree_build(const double* X, int64_t N, int leaf_size, otree* t) {
 
 static void tree_free(otree* t) {
     free(t->perm); free(t->Xs); free(t->begin); free(t->end); free(t->lo);
-    free(t->hi); free(t->cen); free(t->diam2); free(t->phil);
+    free(t->hi); free(t->cen); free(t->diam2); free(t->phil); free(t->pphil);
 }
 
 static inline int64_t node_n(const otree* t, int64_t v) { return t->end[v] - t->begin[v]; }
@@ -346,7 +349,7 @@ static int mc_point(osolve* S, const int64_t P[3], int slot, int64_t x, double T
         double dlt = f - mean;
         mean += dlt / m;
         m2 += dlt * (f - mean);
-        if (m >= 2) {
+        if (m >= 2 && (m >= 30 || m >= S->m_limit)) { /* the loop can only end here */
             double sig = sqrt(m2 / (m - 1)) / sqrt((double)m);
             double lhs = S->z * sig, rhs;
             double lb = phil - Ti * (fabs(mean) + S->z * sig);
@@ -439,7 +442,7 @@ static int try_summarize(osolve* S, const int64_t P[3]) {
             for (int s = 0; s < 3 && ok; ++s) {
                 if (!first[s]) continue;
                 for (int64_t x = t->begin[P[s]]; x < t->end[P[s]]; ++x) {
-                    if (!mc_point(S, P, s, x, T[s], t->phil[P[s]], &est[q++])) { ok = 0; break; }
+                    if (!mc_point(S, P, s, x, T[s], t->pphil[x], &est[q++])) { ok = 0; break; }
                 }
             }
             if (ok) { /* Algorithm 5 */
@@ -507,6 +510,8 @@ static void seed_phil(otree* t, int seed_up) {
                     seed[i] += f; seed[j] += f; seed[k] += f;
                 }
     }
+    t->pphil = (double*)malloc(sizeof(double) * (size_t)N);
+    for (int64_t p = 0; p < N; ++p) t->pphil[p] = fabs(seed[p]);
     for (int64_t v = 0; v < t->n_nodes; ++v) {
         double m = INFINITY;
         for (int64_t p = t->begin[v]; p < t->end[v]; ++p) if (fabs(seed[p]) < m) m = fabs(seed[p]);

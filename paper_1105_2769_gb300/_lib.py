@@ -76,6 +76,7 @@ SIGNATURES = {
     "mbm_tree_info": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                              ctypes.POINTER(ctypes.c_int32)]),
     "mbm_tree_export": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mbm_potential_sampled": (_int, [_vp, _vp, _i64, _vp, _i64, _vp, _vp]),
 }
 OPTIONAL = {}
 

@@ -193,6 +193,21 @@ def potential_host(X: np.ndarray, eps: float = 0.0, alpha: float = 0.0, mode="fp
     return phi
 
 
+def potential_sampled(X: torch.Tensor, idx, ctx: Context | None = None) -> torch.Tensor:
+    """Exact Phi (FP32 bulk, FP64 accumulation) of the particles idx only."""
+    X = _check_points(X)
+    n = X.shape[0]
+    idx_t = torch.as_tensor(np.asarray(idx, dtype=np.int64), device=X.device)
+    if idx_t.numel() and (int(idx_t.min()) < 0 or int(idx_t.max()) >= n):
+        raise IndexError("particle index out of range")
+    ctx = ctx or default_context(X.device.index)
+    out = torch.empty(idx_t.numel(), dtype=torch.float64, device=X.device)
+    _lib.check(_lib.load().mbm_potential_sampled(ctx.handle, ctypes.c_void_p(X.data_ptr()), n,
+                                                 ctypes.c_void_p(idx_t.data_ptr()), idx_t.numel(),
+                                                 ctypes.c_void_p(out.data_ptr()), _stream_handle()))
+    return out
+
+
 def forces(X: torch.Tensor, mode="fp32", eps: float = 0.0, alpha: float = 0.0,
            ctx: Context | None = None) -> torch.Tensor:
     """F_i = -dE/dx_i, E = sum over unordered triples of phi."""

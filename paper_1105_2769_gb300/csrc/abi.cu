@@ -35,11 +35,11 @@ extern "C" void mbm_config_default(mbm_config* cfg) {
     cfg->tau = 0.0;
     cfg->leaf_size = 32;
     cfg->m_limit = 256;
-    cfg->zeta = 4.0;
+    cfg->zeta = 32.0;
     cfg->seed = 0x5eed5eedULL;
     cfg->mc_rule = 0;
     cfg->validate = 1;
-    cfg->seed_levels = 2;
+    cfg->seed_levels = 3;
     cfg->tuple_counts = nullptr;
 }
 
@@ -150,7 +150,9 @@ extern "C" mbm_status mbm_ctx_set_timing(mbm_ctx* ctx, int enable) {
 }
 
 extern "C" double mbm_ctx_last_kernel_ms(mbm_ctx* ctx) {
-    if (!ctx || !ctx->timed) return -1.0;
+    if (!ctx) return -1.0;
+    if (ctx->timed_ms >= 0.0) return ctx->timed_ms;
+    if (!ctx->timed) return -1.0;
     if (cudaEventSynchronize(ctx->ev1) != cudaSuccess) return -1.0;
     float ms = -1.f;
     if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) != cudaSuccess) return -1.0;
@@ -161,7 +163,13 @@ void mbm_time_begin(mbm_ctx* ctx, cudaStream_t s) {
     if (ctx->timing) {
         cudaEventRecord(ctx->ev0, s);
         ctx->timed = false;
+        ctx->timed_ms = -1.0;
     }
+}
+
+void mbm_time_set_ms(mbm_ctx* ctx, double ms) {
+    ctx->timed = false;
+    ctx->timed_ms = ms;
 }
 
 void mbm_time_end(mbm_ctx* ctx, cudaStream_t s) {
@@ -280,4 +288,28 @@ extern "C" mbm_status mbm_potential_host(mbm_ctx* ctx, const double* X_host, int
     if (e != cudaSuccess && st == MBM_OK) st = mbm_cuda_fail(e, "cudaStreamSynchronize");
     mbm_budget_release(ctx, xb + pb);
     return st;
+}
+
+extern "C" mbm_status mbm_potential_sampled(mbm_ctx* ctx, const double* X_dev, int64_t N,
+                                            const int64_t* idx_dev, int64_t n_idx,
+                                            double* out_dev, mbm_stream_t stream) {
+    MBM_TRY(check_common(ctx, X_dev, N, out_dev));
+    if (n_idx < 0 || n_idx > (1 << 20)) return mbm_fail(MBM_EINVAL, "n_idx must be in [0, 2^20]");
+    if (n_idx > 0 && !idx_dev) return mbm_fail(MBM_EINVAL, "NULL idx");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    MBM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (n_idx == 0) return MBM_OK;
+    MBM_CUDA_TRY(cudaMemsetAsync(out_dev, 0, (size_t)n_idx * sizeof(double), s));
+    if (N < 3) return MBM_OK;
+    MBM_TRY(mbm_scratch_reserve(ctx, 256 + (size_t)N * 2 * sizeof(float4)));
+    char* base = static_cast<char*>(ctx->scratch);
+    auto* xh = reinterpret_cast<float4*>(base + 256);
+    auto* xl = xh + N;
+    MBM_CUDA_TRY(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+    MBM_CUDA_TRY(launch_pack_hilo(X_dev, N, xh, xl, ctx->d_flags, s));
+    mbm_time_begin(ctx, s);
+    MBM_CUDA_TRY(launch_sampled_fp32(xh, xl, N, idx_dev, n_idx, out_dev, ctx->num_sms, s));
+    mbm_time_end(ctx, s);
+    return MBM_OK;
 }

@@ -272,6 +272,58 @@ exh_fp64_kernel(const double4* __restrict__ x4, int N, int NT, long long n_items
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exact Phi (FP32 bulk) for a sample of particles: every pair j < k of the
+// set against each sampled particle i (pairs containing i drop out because
+// their distance is exactly zero). A warp owns one tile pair (J, K) with its
+// own table; lanes are the sampled particles.
+// ---------------------------------------------------------------------------
+struct SampleWarpSmem {
+    mbm_tile::TabPair tab[kTile][kTile / 2];
+    float4 sJh[kTile], sJl[kTile], sKh[kTile], sKl[kTile];
+    float redJ[kTile][kTile + 1];
+    float redK[kTile][kTile + 1];
+};
+constexpr int kSampleWarps = 4;
+
+__global__ void __launch_bounds__(kSampleWarps * 32)
+sampled_fp32_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int N, int NT,
+                    const int64_t* __restrict__ idx, int n_idx, double* __restrict__ out,
+                    long long n_items) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SampleWarpSmem& w = reinterpret_cast<SampleWarpSmem*>(smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; t < n_items;
+         t += warps) {
+        int J, K;
+        decode_pair_item(t, NT, J, K);
+        const int nJ = min(kTile, N - J * kTile), nK = min(kTile, N - K * kTile);
+        w.sJh[lane] = lane < nJ ? xh[J * kTile + lane] : z4;
+        w.sJl[lane] = lane < nJ ? xl[J * kTile + lane] : z4;
+        w.sKh[lane] = lane < nK ? xh[K * kTile + lane] : z4;
+        w.sKl[lane] = lane < nK ? xl[K * kTile + lane] : z4;
+        __syncwarp();
+        for (int e = lane; e < kTile * kTile; e += 32) {
+            const int jj = e >> 5, kk = e & 31;
+            mbm_tile::build_table_entry(w.tab, jj, kk, w.sJh[jj], w.sJl[jj], w.sKh[kk], w.sKl[kk],
+                                        jj < nJ && kk < nK && (J != K || jj < kk));
+        }
+        __syncwarp();
+        for (int q0 = 0; q0 < n_idx; q0 += kTile) {
+            const int q = q0 + lane;
+            const bool iv = q < n_idx;
+            const int64_t i = iv ? idx[q] : 0;
+            const float4 ih = iv ? xh[i] : z4, il = iv ? xl[i] : z4;
+            const float acc = mbm_tile::tile_triples(w.tab, w.sJh, w.sJl, w.sKh, w.sKl, ih, il, iv,
+                                                     lane, nJ, nK, false, false, w.redJ, w.redK);
+            if (iv) atomicAdd(&out[q], (double)acc);
+        }
+        __syncwarp();
+    }
+}
+
 int grid_for(const void* kernel, int threads, size_t smem, int num_sms, long long items) {
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) !=
@@ -329,5 +381,22 @@ cudaError_t launch_exh_fp64(const double4* x4, int64_t N, double* phi, unsigned 
     if (e != cudaSuccess) return e;
     const int grid = grid_for((const void*)exh_fp64_kernel, threads, smem, num_sms, items);
     exh_fp64_kernel<<<grid, threads, smem, s>>>(x4, (int)N, NT, items, counter, phi, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sampled_fp32(const float4* xhi, const float4* xlo, int64_t N,
+                                const int64_t* idx, int64_t n_idx, double* out, int num_sms,
+                                cudaStream_t s) {
+    const int NT = (int)((N + kTile - 1) / kTile);
+    const long long items = (long long)NT * (NT + 1) / 2;
+    const int threads = kSampleWarps * 32;
+    const size_t smem = sizeof(SampleWarpSmem) * kSampleWarps;
+    cudaError_t e = cudaFuncSetAttribute((const void*)sampled_fp32_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for((const void*)sampled_fp32_kernel, threads, smem, num_sms,
+                              (items + kSampleWarps - 1) / kSampleWarps);
+    sampled_fp32_kernel<<<grid, threads, smem, s>>>(xhi, xlo, (int)N, NT, idx, (int)n_idx, out,
+                                                    items);
     return cudaGetLastError();
 }

@@ -51,12 +51,15 @@ struct mbm_ctx {
     std::mutex mu;           // one solve at a time per context
     bool timing = false;     // record events around the dominant kernel
     bool timed = false;      // the last solve recorded events
+    double timed_ms = -1.0;  // >= 0: the last solve's dominant-kernel time, summed
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 // Event helpers: no-ops unless ctx->timing.
 void mbm_time_begin(mbm_ctx* ctx, cudaStream_t s);
 void mbm_time_end(mbm_ctx* ctx, cudaStream_t s);
+// Report an already summed dominant-kernel time for the last solve.
+void mbm_time_set_ms(mbm_ctx* ctx, double ms);
 
 // Make sure the arena holds at least `bytes`; may reallocate (synchronous).
 mbm_status mbm_scratch_reserve(mbm_ctx* ctx, size_t bytes);
@@ -84,3 +87,7 @@ cudaError_t launch_exh_fp32(const float4* xhi, const float4* xlo, int64_t N, dou
                             cudaStream_t s);
 cudaError_t launch_exh_fp64(const double4* x4, int64_t N, double* phi, unsigned long long* counter,
                             int* flags, int num_sms, cudaStream_t s);
+// Exact FP32-bulk Phi of sampled particles idx[0..n_idx) (out zeroed by the caller).
+cudaError_t launch_sampled_fp32(const float4* xhi, const float4* xlo, int64_t N,
+                                const int64_t* idx, int64_t n_idx, double* out, int num_sms,
+                                cudaStream_t s);

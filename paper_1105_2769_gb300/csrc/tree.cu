@@ -55,6 +55,8 @@ struct mbm_tree {
     double* ncen = nullptr;
     double* ndiam2 = nullptr; // per node
     double* nphil = nullptr;  // per node
+    double* pphil = nullptr;  // per sorted particle: |S(x)|
+    int* weak = nullptr;      // per node: up to 32 sorted positions of smallest Phi^l(x)
 };
 
 namespace {
@@ -295,7 +297,8 @@ seed_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_
 // Base cases: leaf triples from the traversal's base list.
 __global__ void __launch_bounds__(kRangeWarps * 32)
 base_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_t N,
-            const int4* __restrict__ items, int64_t n_items, double* acc, int* flags) {
+            const int4* __restrict__ items, int64_t n_items, double* acc, int* flags,
+            unsigned long long* n_triples) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem& w = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
     const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -307,6 +310,15 @@ base_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_
     node_range(t.z, N, b3, e3);
     range_triple(w, xh, xl, b1, (int)(e1 - b1), b2, (int)(e2 - b2), b3, (int)(e3 - b3), t.x == t.y,
                  t.y == t.z, t.x == t.z, acc, flags);
+    if ((threadIdx.x & 31) == 0) {  // point triples of this leaf triple (Fig. 4 cases)
+        const unsigned long long n1 = e1 - b1, n2 = e2 - b2, n3 = e3 - b3;
+        unsigned long long c;
+        if (t.x == t.y && t.y == t.z) c = n1 * (n1 - 1) * (n1 - 2) / 6;
+        else if (t.x == t.y) c = n1 * (n1 - 1) / 2 * n3;
+        else if (t.y == t.z) c = n1 * (n2 * (n2 - 1) / 2);
+        else c = n1 * n2 * n3;
+        atomicAdd(n_triples, c);
+    }
 }
 
 // Tuple counts of base cases by enumeration (validation only).
@@ -334,7 +346,7 @@ __global__ void base_count_kernel(int64_t N, const int4* __restrict__ items, int
 
 // Phi^l per node: |seed| per particle, min over leaves, then up the tree.
 __global__ void phil_leaf_kernel(const double* __restrict__ seed, int64_t N, int64_t first_leaf,
-                                 int64_t n_leaves, double* nphil) {
+                                 int64_t n_leaves, double* nphil, double* pphil) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (w >= n_leaves) return;
@@ -342,8 +354,53 @@ __global__ void phil_leaf_kernel(const double* __restrict__ seed, int64_t N, int
     int64_t b, e;
     node_range(v, N, b, e);
     double m = b + lane < e ? fabs(seed[b + lane]) : INFINITY;
+    if (b + lane < e) pphil[b + lane] = m;
     for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) nphil[v] = b < e ? m : 0.0;
+}
+
+// Per leaf: its particles in ascending Phi^l(x) (ties by position), padded with -1.
+__global__ void weak_leaf_kernel(const double* __restrict__ pphil, int64_t N, int64_t first_leaf,
+                                 int64_t n_leaves, int* weak) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (w >= n_leaves) return;
+    const int64_t v = first_leaf + w;
+    int64_t b, e;
+    node_range(v, N, b, e);
+    const bool in = b + lane < e;
+    const double key = in ? pphil[b + lane] : INFINITY;
+    int rank = 0;  // rank of this lane's particle by (key, position)
+    for (int o = 0; o < 32; ++o) {
+        const double k2 = __shfl_sync(0xffffffffu, key, o);
+        const bool in2 = __shfl_sync(0xffffffffu, (int)in, o) != 0;
+        if (in2 && (k2 < key || (k2 == key && o < lane))) ++rank;
+    }
+    weak[v * 32 + lane] = -1;
+    __syncwarp();
+    if (in) weak[v * 32 + rank] = (int)(b + lane);
+}
+
+// Per internal node: the 32 smallest of its children's lists (merge).
+__global__ void weak_internal_kernel(int64_t first, int64_t count, const double* __restrict__ pphil,
+                                     int* weak) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const int64_t v = first + t;
+    const int* A = weak + (2 * v + 1) * 32;
+    const int* Bl = weak + (2 * v + 2) * 32;
+    int ia = 0, ib = 0;
+    for (int o = 0; o < 32; ++o) {
+        const int a = ia < 32 ? A[ia] : -1, b = ib < 32 ? Bl[ib] : -1;
+        int pick;
+        if (a < 0 && b < 0) pick = -1;
+        else if (b < 0) pick = a;
+        else if (a < 0) pick = b;
+        else pick = (pphil[a] < pphil[b] || (pphil[a] == pphil[b] && a < b)) ? a : b;
+        if (pick >= 0 && pick == a) ++ia;
+        else if (pick >= 0) ++ib;
+        weak[v * 32 + o] = pick;
+    }
 }
 
 __global__ void phil_internal_kernel(int64_t first, int64_t count, double* nphil) {
@@ -358,7 +415,8 @@ __global__ void phil_internal_kernel(int64_t first, int64_t count, double* nphil
 // ---------------------------------------------------------------------------
 struct Trav {
     int64_t N, n_nodes, n_leaves;
-    const double *nlo, *nhi, *ncen, *ndiam2, *nphil;
+    const double *nlo, *nhi, *ncen, *ndiam2, *nphil, *pphil;
+    const int* weak;
     const double* xs;
     const float4 *xh, *xl;
     double eps, tau, troot, zeta, z, alpha;
@@ -733,59 +791,15 @@ __device__ __forceinline__ void candidate_point(const Trav& p, const int64_t P[3
     x = 0;
 }
 
-__global__ void mc_sizes_kernel(const int4* __restrict__ mc, int64_t n_mc, int64_t N,
-                                int64_t* chunks) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= n_mc) return;
-    const int4 t = mc[c];
-    const int64_t P[3] = {t.x, t.y, t.z};
-    int64_t U = 0;
-    for (int s = 0; s < 3; ++s) {
-        if (s > 0 && P[s] == P[s - 1]) continue;
-        int64_t b, e;
-        node_range(P[s], N, b, e);
-        U += e - b;
-    }
-    chunks[c] = (U + 31) / 32;
-}
 
-// One warp per 32-particle chunk of a candidate (Algorithm 4 per particle).
-__global__ void mc_kernel(const int4* __restrict__ mc, int64_t c0, int64_t n_c,
-                          const int64_t* __restrict__ chunk_off /* exclusive, n_c + 1 */,
-                          int* cand_fail, double* est, Trav p) {
+// Algorithm 4 for up to 32 particles of candidate P, one per lane. A
+// particle that fails sets *fail; all lanes stop once *fail is set (Algorithm 3
+// returns false at the first failing particle). Returns T_i * mean.
+__device__ double mc_warp(const Trav& p, const int64_t P[3], const int64_t bb[3],
+                          const int64_t nn[3], bool active, int slot, int64_t x, double Ti,
+                          volatile int* fail) {
     const int lane = threadIdx.x & 31;
-    const int64_t rel = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (rel >= chunk_off[n_c] - chunk_off[0]) return;
-    const int64_t chunk = chunk_off[0] + rel;
-    int64_t lo = 0, hi = n_c;  // largest c with chunk_off[c] <= chunk
-    while (hi - lo > 1) {
-        const int64_t mid = (lo + hi) / 2;
-        if (chunk_off[mid] <= chunk) lo = mid;
-        else hi = mid;
-    }
-    const int64_t c = lo;
-    volatile int* fail = cand_fail + c;
-    if (*fail) return;  // warp-uniform
-    const int4 t = mc[c0 + c];
-    const int64_t P[3] = {t.x, t.y, t.z};
-    double n[3], T[3];
-    bool first[3];
-    triple_counts(p, P, n, T, first);
-    int64_t bb[3], nn[3];
-    int64_t U = 0;
-    for (int s = 0; s < 3; ++s) {
-        int64_t e;
-        node_range(P[s], p.N, bb[s], e);
-        nn[s] = e - bb[s];
-        if (first[s]) U += nn[s];
-    }
-    const int64_t u = (chunk - chunk_off[c]) * 32 + lane;
-    const bool active = u < U;
-    int slot = 0;
-    int64_t x = 0;
-    if (active) candidate_point(p, P, u, slot, x);
-    const double Ti = T[slot];
-    const double phil = p.nphil[P[slot]];
+    const double phil = active ? p.pphil[x] : 0.0;  // the particle's own Phi^l
     double mean = 0.0, m2 = 0.0;
     int m = 0;
     bool pass = false, done = !active;
@@ -804,7 +818,7 @@ __global__ void mc_kernel(const int4* __restrict__ mc, int64_t c0, int64_t n_c,
             const double dlt = __dsub_rn(f, mean);
             mean = __dadd_rn(mean, __ddiv_rn(dlt, (double)m));
             m2 = __dadd_rn(m2, __dmul_rn(dlt, __dsub_rn(f, mean)));
-            if (m >= 2) {
+            if (m >= 2 && (m >= 30 || m >= p.m_limit)) {  // the test can end the loop only here
                 const double sig =
                     __ddiv_rn(__dsqrt_rn(__ddiv_rn(m2, (double)(m - 1))), __dsqrt_rn((double)m));
                 const double lhs = __dmul_rn(p.z, sig);
@@ -816,7 +830,7 @@ __global__ void mc_kernel(const int4* __restrict__ mc, int64_t c0, int64_t n_c,
                         : __ddiv_rn(__dadd_rn(__dmul_rn(p.eps, lb), p.tau), p.troot);
                 pass = lhs <= rhs;
                 if ((pass && m >= 30) || m >= p.m_limit) done = true;
-            } else if (m >= p.m_limit) {
+            } else if (m >= p.m_limit) {  // m_limit < 2
                 pass = false;
                 done = true;
             }
@@ -827,10 +841,97 @@ __global__ void mc_kernel(const int4* __restrict__ mc, int64_t c0, int64_t n_c,
             if (__shfl_sync(0xffffffffu, f, 0)) break;
         }
     }
-    if (active) est[rel * 32 + lane] = __dmul_rn(Ti, mean);
     int tot = samples;
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (lane == 0 && tot) atomicAdd(&p.stat[5], (ull)tot);
+    return __dmul_rn(Ti, mean);
+}
+
+__device__ __forceinline__ void candidate_geometry(const Trav& p, const int64_t P[3], double T[3],
+                                                   bool first[3], int64_t bb[3], int64_t nn[3],
+                                                   int64_t& U) {
+    double n[3];
+    triple_counts(p, P, n, T, first);
+    U = 0;
+    for (int s = 0; s < 3; ++s) {
+        int64_t e;
+        node_range(P[s], p.N, bb[s], e);
+        nn[s] = e - bb[s];
+        if (first[s]) U += nn[s];
+    }
+}
+
+// Probe: each distinct node's particles with the smallest Phi^l(x) first
+// (the likeliest to fail); a warp per (candidate, slot).
+__global__ void mc_probe_kernel(const int4* __restrict__ mc, int64_t n_c, int* cand_fail, Trav p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (w >= n_c * 3) return;
+    const int64_t c = w / 3;
+    const int slot = (int)(w % 3);
+    const int4 t = mc[c];
+    const int64_t P[3] = {t.x, t.y, t.z};
+    if (slot > 0 && P[slot] == P[slot - 1]) return;
+    volatile int* fail = cand_fail + c;
+    if (*fail) return;
+    double T[3];
+    bool first[3];
+    int64_t bb[3], nn[3], U;
+    candidate_geometry(p, P, T, first, bb, nn, U);
+    const int x = p.weak[P[slot] * 32 + lane];
+    mc_warp(p, P, bb, nn, x >= 0, slot, x >= 0 ? x : 0, T[slot], fail);
+}
+
+__global__ void mc_sizes_kernel(const int4* __restrict__ mc, int64_t n_mc, int64_t N,
+                                const int* __restrict__ cand_fail, int64_t* chunks) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= n_mc) return;
+    if (cand_fail[c]) {
+        chunks[c] = 0;
+        return;
+    }
+    const int4 t = mc[c];
+    const int64_t P[3] = {t.x, t.y, t.z};
+    int64_t U = 0;
+    for (int s = 0; s < 3; ++s) {
+        if (s > 0 && P[s] == P[s - 1]) continue;
+        int64_t b, e;
+        node_range(P[s], N, b, e);
+        U += e - b;
+    }
+    chunks[c] = (U + 31) / 32;
+}
+
+// One warp per 32-particle chunk of a candidate that passed the probe.
+__global__ void mc_kernel(const int4* __restrict__ mc, int64_t c0, int64_t n_c,
+                          const int64_t* __restrict__ chunk_off /* exclusive, n_c + 1 */,
+                          int* cand_fail, double* est, Trav p) {
+    const int lane = threadIdx.x & 31;
+    const int64_t rel = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (rel >= chunk_off[n_c] - chunk_off[0]) return;
+    const int64_t chunk = chunk_off[0] + rel;
+    int64_t lo = 0, hi = n_c;  // largest c with chunk_off[c] <= chunk
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) / 2;
+        if (chunk_off[mid] <= chunk) lo = mid;
+        else hi = mid;
+    }
+    const int64_t c = lo;
+    volatile int* fail = cand_fail + c;
+    if (*fail) return;  // warp-uniform
+    const int4 t = mc[c0 + c];
+    const int64_t P[3] = {t.x, t.y, t.z};
+    double T[3];
+    bool first[3];
+    int64_t bb[3], nn[3], U;
+    candidate_geometry(p, P, T, first, bb, nn, U);
+    const int64_t u = (chunk - chunk_off[c]) * 32 + lane;
+    const bool active = u < U;
+    int slot = 0;
+    int64_t x = 0;
+    if (active) candidate_point(p, P, u, slot, x);
+    const double e = mc_warp(p, P, bb, nn, active, slot, x, T[slot], fail);
+    if (active) est[rel * 32 + lane] = e;
 }
 
 // Algorithm 5 for passing candidates; failing ones go on to base/split.
@@ -978,7 +1079,8 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
     const std::vector<size_t> parts = {
         (size_t)N * 8, (size_t)N * 24, (size_t)N * 16, (size_t)N * 16,  // perm xs xh xl
         (size_t)n_nodes * 24, (size_t)n_nodes * 24, (size_t)n_nodes * 24,  // lo hi cen
-        (size_t)n_nodes * 8, (size_t)n_nodes * 8};                          // diam2 phil
+        (size_t)n_nodes * 8, (size_t)n_nodes * 8, (size_t)N * 8,           // diam2 phil pphil
+        (size_t)n_nodes * 32 * 4};                                          // weak
     t->bytes = carve_size(parts);
     mbm_status st = mbm_budget_charge(ctx, t->bytes);
     if (st != MBM_OK) {
@@ -1001,6 +1103,8 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
     t->ncen = cv.take<double>(3 * n_nodes);
     t->ndiam2 = cv.take<double>(n_nodes);
     t->nphil = cv.take<double>(n_nodes);
+    t->pphil = cv.take<double>(N);
+    t->weak = cv.take<int>((size_t)n_nodes * 32);
 
     // Temporary scratch: box partials, keys/indices (double-buffered), CUB temp, seed sums.
     const int nb = 256;
@@ -1080,10 +1184,16 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
                   kRangeWarps * 32, wsm, s>>>(t->xh, t->xl, N, sd, n_seed_nodes, combos,
                                               (int)cmb.size(), seed, ctx->d_flags);
     phil_leaf_kernel<<<grid_of(n_leaves * 32, 256), 256, 0, s>>>(seed, N, first_leaf, n_leaves,
-                                                                 t->nphil);
+                                                                 t->nphil, t->pphil);
     for (int d = depth - 1; d >= 0; --d) {
         const int64_t first = ((int64_t)1 << d) - 1, cnt = (int64_t)1 << d;
         phil_internal_kernel<<<grid_of(cnt, 256), 256, 0, s>>>(first, cnt, t->nphil);
+    }
+    weak_leaf_kernel<<<grid_of(n_leaves * 32, 256), 256, 0, s>>>(t->pphil, N, first_leaf, n_leaves,
+                                                                 t->weak);
+    for (int d = depth - 1; d >= 0; --d) {
+        const int64_t first = ((int64_t)1 << d) - 1, cnt = (int64_t)1 << d;
+        weak_internal_kernel<<<grid_of(cnt, 256), 256, 0, s>>>(first, cnt, t->pphil, t->weak);
     }
     TRY_LAUNCH();
 #undef TRY_LAUNCH
@@ -1193,193 +1303,217 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
 
     const int64_t n_nodes = tree->n_nodes, n_leaves = tree->n_leaves;
     const bool counting = cfg.tuple_counts != nullptr;
-    int64_t cap_front = std::max<int64_t>(1 << 16, 4 * N), cap_mc = std::max<int64_t>(1 << 14, N / 4);
-    int64_t cap_base = std::max<int64_t>(1 << 18, 8 * N), cap_est = std::max<int64_t>(1 << 20, 8 * N);
+    // Frontier chunk B: a chunk of B node triples yields at most 4B children,
+    // B Monte Carlo candidates and B base cases, so no list can overflow.
+    const int64_t B = std::max<int64_t>(1 << 14, std::min<int64_t>(1 << 20, 2 * N));
+    const int max_levels = 3 * tree->depth + 8;
+    const int64_t cap_lvl = 4 * B, cap_mc = B;
+    const int64_t cap_base = std::max<int64_t>(4 * B, 1 << 22);
+    const int64_t cap_est = 3 * N + 64 * 1024;
     const double z = z_two_sided(alpha);
 
-    for (int attempt = 0; attempt < 6; ++attempt) {
-        const std::vector<size_t> parts = {
-            (size_t)N * 8,           (size_t)n_nodes * 8,                    // pt_acc node_acc
-            counting ? (size_t)N * 8 : 0, counting ? (size_t)n_nodes * 8 : 0,  // counts
-            (size_t)cap_front * 16,  (size_t)cap_front * 16,                 // front next
-            (size_t)cap_mc * 16,     (size_t)cap_base * 16,                  // mc base
-            (size_t)cap_mc * 8 + 16, (size_t)cap_mc * 4,                     // chunk_off fail
-            (size_t)cap_est * 8,     256,                                    // est, counters
-            4096};
-        size_t cub_bytes = 0;
-        cub::DeviceScan::ExclusiveSum(nullptr, cub_bytes, (int64_t*)nullptr, (int64_t*)nullptr,
-                                      (int)(cap_mc + 1), s);
-        std::vector<size_t> all = parts;
-        all.push_back(cub_bytes);
-        MBM_TRY(mbm_scratch_reserve(ctx, carve_size(all)));
-        Carve sc{static_cast<char*>(ctx->scratch)};
-        double* pt_acc = sc.take<double>(N);
-        double* node_acc = sc.take<double>(n_nodes);
-        ull* pt_cnt = counting ? sc.take<ull>(N) : nullptr;
-        ull* node_cnt = counting ? sc.take<ull>(n_nodes) : nullptr;
-        int4* front = sc.take<int4>(cap_front);
-        int4* next = sc.take<int4>(cap_front);
-        int4* mcl = sc.take<int4>(cap_mc);
-        int4* basel = sc.take<int4>(cap_base);
-        int64_t* chunk_off = sc.take<int64_t>(cap_mc + 2);
-        int* cand_fail = sc.take<int>(cap_mc);
-        double* est = sc.take<double>(cap_est);
-        ull* ctr = sc.take<ull>(32);  // 0 n_next 1 n_mc 2 n_base 3.. stats
-        sc.take<char>(4096);
-        void* cub_tmp = sc.take<char>(cub_bytes);
-        ull* h = reinterpret_cast<ull*>(ctx->h_flags) + 8;  // pinned, after the status word
+    size_t cub_bytes = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, cub_bytes, (int64_t*)nullptr, (int64_t*)nullptr,
+                                  (int)(cap_mc + 1), s);
+    const std::vector<size_t> parts = {
+        (size_t)N * 8, (size_t)n_nodes * 8,                                // pt_acc node_acc
+        counting ? (size_t)N * 8 : 0, counting ? (size_t)n_nodes * 8 : 0,  // counts
+        (size_t)max_levels * cap_lvl * 16,                                 // level buffers
+        (size_t)cap_mc * 16, (size_t)cap_base * 16,                        // mc, base
+        (size_t)(cap_mc + 2) * 8, (size_t)cap_mc * 4,                      // chunk_off, fail
+        (size_t)cap_est * 8, 256, cub_bytes};                              // est, counters
+    MBM_TRY(mbm_scratch_reserve(ctx, carve_size(parts)));
+    Carve sc{static_cast<char*>(ctx->scratch)};
+    double* pt_acc = sc.take<double>(N);
+    double* node_acc = sc.take<double>(n_nodes);
+    ull* pt_cnt = counting ? sc.take<ull>(N) : nullptr;
+    ull* node_cnt = counting ? sc.take<ull>(n_nodes) : nullptr;
+    int4* lvl = sc.take<int4>((size_t)max_levels * cap_lvl);
+    int4* mcl = sc.take<int4>(cap_mc);
+    int4* basel = sc.take<int4>(cap_base);
+    int64_t* chunk_off = sc.take<int64_t>(cap_mc + 2);
+    int* cand_fail = sc.take<int>(cap_mc);
+    double* est = sc.take<double>(cap_est);
+    ull* ctr = sc.take<ull>(32);  // 0 n_next, 1 n_mc, 2 n_base, 3.. statistics
+    void* cub_tmp = sc.take<char>(cub_bytes);
+    ull* h = reinterpret_cast<ull*>(ctx->h_flags) + 8;  // pinned, after the status word
 
-        MBM_CUDA_TRY(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
-        MBM_CUDA_TRY(cudaMemsetAsync(pt_acc, 0, (size_t)N * 8, s));
-        MBM_CUDA_TRY(cudaMemsetAsync(node_acc, 0, (size_t)n_nodes * 8, s));
-        if (counting) {
-            MBM_CUDA_TRY(cudaMemsetAsync(pt_cnt, 0, (size_t)N * 8, s));
-            MBM_CUDA_TRY(cudaMemsetAsync(node_cnt, 0, (size_t)n_nodes * 8, s));
+    MBM_CUDA_TRY(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+    MBM_CUDA_TRY(cudaMemsetAsync(pt_acc, 0, (size_t)N * 8, s));
+    MBM_CUDA_TRY(cudaMemsetAsync(node_acc, 0, (size_t)n_nodes * 8, s));
+    if (counting) {
+        MBM_CUDA_TRY(cudaMemsetAsync(pt_cnt, 0, (size_t)N * 8, s));
+        MBM_CUDA_TRY(cudaMemsetAsync(node_cnt, 0, (size_t)n_nodes * 8, s));
+    }
+    MBM_CUDA_TRY(cudaMemsetAsync(ctr, 0, 32 * sizeof(ull), s));
+    const int4 root = make_int4(0, 0, 0, 0);
+    MBM_CUDA_TRY(cudaMemcpyAsync(lvl, &root, sizeof(int4), cudaMemcpyHostToDevice, s));
+
+    Trav p;
+    p.N = N;
+    p.n_nodes = n_nodes;
+    p.n_leaves = n_leaves;
+    p.nlo = tree->nlo;
+    p.nhi = tree->nhi;
+    p.ncen = tree->ncen;
+    p.ndiam2 = tree->ndiam2;
+    p.nphil = tree->nphil;
+    p.pphil = tree->pphil;
+    p.weak = tree->weak;
+    p.xs = tree->xs;
+    p.xh = tree->xh;
+    p.xl = tree->xl;
+    p.eps = absolute ? 0.0 : eps;
+    p.tau = absolute ? eps : cfg.tau;
+    p.troot = (double)(N - 1) * (double)(N - 2) * 0.5;
+    p.zeta = cfg.zeta;
+    p.z = z;
+    p.alpha = alpha;
+    p.m_limit = cfg.m_limit;
+    p.mc_rule = cfg.mc_rule;
+    p.key0 = (uint32_t)cfg.seed;
+    p.key1 = (uint32_t)(cfg.seed >> 32);
+    p.node_acc = node_acc;
+    p.pt_acc = pt_acc;
+    p.node_cnt = node_cnt;
+    p.pt_cnt = pt_cnt;
+    p.n_next = ctr + 0;
+    p.n_mc = ctr + 1;
+    p.n_base = ctr + 2;
+    p.stat = ctr + 3;
+    p.cap_next = cap_lvl;
+    p.cap_mc = cap_mc;
+    p.cap_base = cap_base;
+    p.mc = mcl;
+    p.base = basel;
+    p.flags = ctx->d_flags;
+
+    const size_t wsm = sizeof(WarpSmem) * kRangeWarps;
+    MBM_CUDA_TRY(cudaFuncSetAttribute((const void*)base_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+    // Base cases run whenever the list could not take another chunk (Phi^l is
+    // fixed, so base cases may run in any order); their time is accumulated.
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> base_ev;
+    int64_t total_base = 0;
+    auto flush_base = [&](int64_t n) -> mbm_status {
+        if (n <= 0) return MBM_OK;
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (tm.on) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, s);
         }
-        MBM_CUDA_TRY(cudaMemsetAsync(ctr, 0, 32 * sizeof(ull), s));
-        const int4 root = make_int4(0, 0, 0, 0);
-        MBM_CUDA_TRY(cudaMemcpyAsync(front, &root, sizeof(int4), cudaMemcpyHostToDevice, s));
-
-        Trav p;
-        p.N = N;
-        p.n_nodes = n_nodes;
-        p.n_leaves = n_leaves;
-        p.nlo = tree->nlo;
-        p.nhi = tree->nhi;
-        p.ncen = tree->ncen;
-        p.ndiam2 = tree->ndiam2;
-        p.nphil = tree->nphil;
-        p.xs = tree->xs;
-        p.xh = tree->xh;
-        p.xl = tree->xl;
-        p.eps = absolute ? 0.0 : eps;
-        p.tau = absolute ? eps : cfg.tau;
-        p.troot = (double)(N - 1) * (double)(N - 2) * 0.5;
-        p.zeta = cfg.zeta;
-        p.z = z;
-        p.alpha = alpha;
-        p.m_limit = cfg.m_limit;
-        p.mc_rule = cfg.mc_rule;
-        p.key0 = (uint32_t)cfg.seed;
-        p.key1 = (uint32_t)(cfg.seed >> 32);
-        p.node_acc = node_acc;
-        p.pt_acc = pt_acc;
-        p.node_cnt = node_cnt;
-        p.pt_cnt = pt_cnt;
-        p.n_next = ctr + 0;
-        p.n_mc = ctr + 1;
-        p.n_base = ctr + 2;
-        p.stat = ctr + 3;
-        p.cap_next = cap_front;
-        p.cap_mc = cap_mc;
-        p.cap_base = cap_base;
-        p.mc = mcl;
-        p.base = basel;
-        p.flags = ctx->d_flags;
-
-        tm.mark(2);
-        int64_t n_front = 1, levels = 0;
-        bool overflow = false;
-        while (n_front > 0) {
-            ++levels;
-            MBM_CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(ull), s));  // n_next, n_mc
-            p.next = next;
-            classify_kernel<<<grid_of(n_front, 256), 256, 0, s>>>(front, n_front, p);
-            MBM_CUDA_TRY(cudaGetLastError());
-            MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 3 * sizeof(ull), cudaMemcpyDeviceToHost, s));
-            MBM_CUDA_TRY(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-            MBM_CUDA_TRY(cudaStreamSynchronize(s));
-            if (ctx->h_flags[0] & MBM_FLAG_OVERFLOW) {
-                overflow = true;
-                break;
-            }
-            const int64_t n_mc = (int64_t)h[1];
-            if (n_mc > 0) {
-                // chunk offsets, then candidates in batches that fit the estimate buffer
-                mc_sizes_kernel<<<grid_of(n_mc, 256), 256, 0, s>>>(mcl, n_mc, N, chunk_off);
-                MBM_CUDA_TRY(cudaMemsetAsync(chunk_off + n_mc, 0, sizeof(int64_t), s));
-                MBM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(cub_tmp, cub_bytes, chunk_off, chunk_off,
-                                                           (int)(n_mc + 1), s));
-                std::vector<int64_t> off(n_mc + 1);
-                MBM_CUDA_TRY(cudaMemcpyAsync(off.data(), chunk_off, (n_mc + 1) * sizeof(int64_t),
-                                             cudaMemcpyDeviceToHost, s));
-                MBM_CUDA_TRY(cudaStreamSynchronize(s));
-                MBM_CUDA_TRY(cudaMemsetAsync(cand_fail, 0, (size_t)n_mc * sizeof(int), s));
-                int64_t c0 = 0;
-                while (c0 < n_mc) {
-                    int64_t c1 = c0 + 1;
-                    while (c1 < n_mc && (off[c1 + 1] - off[c0]) * 32 <= cap_est) ++c1;
-                    if ((off[c1] - off[c0]) * 32 > cap_est) {  // one candidate too large
-                        overflow = true;
-                        break;
-                    }
-                    const int64_t chunks = off[c1] - off[c0];
-                    mc_kernel<<<grid_of(chunks * 32, 256), 256, 0, s>>>(
-                        mcl + c0, 0, c1 - c0, chunk_off + c0, cand_fail + c0, est, p);
-                    mc_commit_kernel<<<(unsigned)(c1 - c0), 256, 0, s>>>(
-                        mcl + c0, 0, c1 - c0, chunk_off + c0, cand_fail + c0, est, p);
-                    MBM_CUDA_TRY(cudaGetLastError());
-                    c0 = c1;
-                }
-                if (overflow) break;
-                MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 3 * sizeof(ull), cudaMemcpyDeviceToHost, s));
-                MBM_CUDA_TRY(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-                MBM_CUDA_TRY(cudaStreamSynchronize(s));
-                if (ctx->h_flags[0] & MBM_FLAG_OVERFLOW) {
-                    overflow = true;
-                    break;
-                }
-            }
-            n_front = (int64_t)h[0];
-            std::swap(front, next);
+        base_kernel<<<grid_of(n * 32, kRangeWarps * 32), kRangeWarps * 32, wsm, s>>>(
+            tree->xh, tree->xl, N, basel, n, pt_acc, ctx->d_flags, ctr + 12);
+        MBM_CUDA_TRY(cudaGetLastError());
+        if (tm.on) {
+            cudaEventRecord(b, s);
+            base_ev.emplace_back(a, b);
         }
-        if (overflow) {
-            MBM_CUDA_TRY(cudaStreamSynchronize(s));
-            cap_front *= 2;
-            cap_mc *= 2;
-            cap_base *= 2;
-            cap_est *= 2;
+        if (counting) base_count_kernel<<<grid_of(n * 32, 256), 256, 0, s>>>(N, basel, n, pt_cnt);
+        total_base += n;
+        return MBM_OK;
+    };
+
+    tm.mark(2);
+    struct Level {
+        int64_t count, done;
+    };
+    std::vector<Level> stack{{1, 0}};
+    int64_t n_base = 0, levels_seen = 1;
+    std::vector<int64_t> off;
+    while (!stack.empty()) {
+        const int li = (int)stack.size() - 1;
+        if (stack[li].done >= stack[li].count) {
+            stack.pop_back();
             continue;
         }
-        tm.mark(3);
-        const int64_t n_base = (int64_t)h[2];
-        if (n_base > 0) {
-            const size_t wsm = sizeof(WarpSmem) * kRangeWarps;
-            cudaFuncSetAttribute((const void*)base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)wsm);
-            mbm_time_begin(ctx, s);
-            base_kernel<<<grid_of(n_base * 32, kRangeWarps * 32), kRangeWarps * 32, wsm, s>>>(
-                tree->xh, tree->xl, N, basel, n_base, pt_acc, ctx->d_flags);
-            mbm_time_end(ctx, s);
-            MBM_CUDA_TRY(cudaGetLastError());
-            if (counting)
-                base_count_kernel<<<grid_of(n_base * 32, 256), 256, 0, s>>>(N, basel, n_base, pt_cnt);
+        if (li + 1 >= max_levels) return mbm_fail(MBM_EOVERFLOW, "traversal deeper than expected");
+        const int64_t take = std::min<int64_t>(B, stack[li].count - stack[li].done);
+        if (n_base + take > cap_base) {
+            MBM_TRY(flush_base(n_base));
+            n_base = 0;
+            MBM_CUDA_TRY(cudaMemsetAsync(ctr + 2, 0, sizeof(ull), s));
         }
-        tm.mark(4);
-        finalize_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, tree->depth, n_nodes, n_leaves, tree->perm,
-                                                        pt_acc, node_acc, pt_cnt, node_cnt, phi,
-                                                        cfg.tuple_counts);
+        int4* cur = lvl + (size_t)li * cap_lvl + stack[li].done;
+        p.next = lvl + (size_t)(li + 1) * cap_lvl;
+        MBM_CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(ull), s));  // n_next, n_mc
+        classify_kernel<<<grid_of(take, 256), 256, 0, s>>>(cur, take, p);
         MBM_CUDA_TRY(cudaGetLastError());
-        tm.mark(5);
-        if (stats) {
-            ull st[9];
-            MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 9 * sizeof(ull), cudaMemcpyDeviceToHost, s));
+        stack[li].done += take;
+        MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 3 * sizeof(ull), cudaMemcpyDeviceToHost, s));
+        MBM_CUDA_TRY(cudaStreamSynchronize(s));
+        const int64_t n_mc = (int64_t)h[1];
+        if (n_mc > 0) {
+            MBM_CUDA_TRY(cudaMemsetAsync(cand_fail, 0, (size_t)n_mc * sizeof(int), s));
+            mc_probe_kernel<<<grid_of(n_mc * 3 * 32, 256), 256, 0, s>>>(mcl, n_mc, cand_fail, p);
+            mc_sizes_kernel<<<grid_of(n_mc, 256), 256, 0, s>>>(mcl, n_mc, N, cand_fail, chunk_off);
+            MBM_CUDA_TRY(cudaMemsetAsync(chunk_off + n_mc, 0, sizeof(int64_t), s));
+            MBM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(cub_tmp, cub_bytes, chunk_off, chunk_off,
+                                                       (int)(n_mc + 1), s));
+            off.resize(n_mc + 1);
+            MBM_CUDA_TRY(cudaMemcpyAsync(off.data(), chunk_off, (n_mc + 1) * sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost, s));
             MBM_CUDA_TRY(cudaStreamSynchronize(s));
-            std::memcpy(st, h, sizeof(st));
-            stats->node_triples_visited = (int64_t)st[3];
-            stats->det_prunes = (int64_t)st[4];
-            stats->mc_prunes = (int64_t)st[5];
-            stats->mc_attempts = (int64_t)st[6];
-            stats->base_cases = (int64_t)st[2];
-            stats->mc_samples = (int64_t)st[8];
-            stats->levels = levels;
-            stats->ms_build = tm.ms(0, 1);
-            stats->ms_traverse = tm.ms(2, 3);
-            stats->ms_base = tm.ms(3, 4);
-            stats->ms_finalize = tm.ms(4, 5);
+            int64_t c0 = 0;
+            while (c0 < n_mc) {  // batches whose estimates fit the buffer
+                int64_t c1 = c0 + 1;
+                while (c1 < n_mc && (off[c1 + 1] - off[c0]) * 32 <= cap_est) ++c1;
+                const int64_t chunks = off[c1] - off[c0];
+                mc_kernel<<<grid_of(chunks * 32, 256), 256, 0, s>>>(mcl + c0, 0, c1 - c0,
+                                                                    chunk_off + c0, cand_fail + c0,
+                                                                    est, p);
+                mc_commit_kernel<<<(unsigned)(c1 - c0), 256, 0, s>>>(
+                    mcl + c0, 0, c1 - c0, chunk_off + c0, cand_fail + c0, est, p);
+                MBM_CUDA_TRY(cudaGetLastError());
+                c0 = c1;
+            }
+            MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 3 * sizeof(ull), cudaMemcpyDeviceToHost, s));
+            MBM_CUDA_TRY(cudaStreamSynchronize(s));
         }
-        if (cfg.validate) return mbm_check_flags(ctx, s);
-        return MBM_OK;
+        n_base = (int64_t)h[2];
+        if (h[0] > 0) {
+            stack.push_back({(int64_t)h[0], 0});
+            levels_seen = std::max<int64_t>(levels_seen, (int64_t)stack.size());
+        }
     }
-    return mbm_fail(MBM_EOVERFLOW, "traversal work lists overflowed after retries");
+    MBM_TRY(flush_base(n_base));
+    tm.mark(3);
+    tm.mark(4);
+    finalize_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, tree->depth, n_nodes, n_leaves, tree->perm,
+                                                    pt_acc, node_acc, pt_cnt, node_cnt, phi,
+                                                    cfg.tuple_counts);
+    MBM_CUDA_TRY(cudaGetLastError());
+    tm.mark(5);
+    double base_ms = 0.0;
+    if (tm.on) {
+        MBM_CUDA_TRY(cudaStreamSynchronize(s));
+        for (auto& ev : base_ev) {
+            float v = 0.f;
+            cudaEventElapsedTime(&v, ev.first, ev.second);
+            base_ms += v;
+            cudaEventDestroy(ev.first);
+            cudaEventDestroy(ev.second);
+        }
+        if (ctx->timing) mbm_time_set_ms(ctx, base_ms);
+    }
+    MBM_CUDA_TRY(cudaMemcpyAsync(ctx->h_flags, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (stats) {
+        MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 13 * sizeof(ull), cudaMemcpyDeviceToHost, s));
+        MBM_CUDA_TRY(cudaStreamSynchronize(s));
+        stats->node_triples_visited = (int64_t)h[3];
+        stats->det_prunes = (int64_t)h[4];
+        stats->mc_prunes = (int64_t)h[5];
+        stats->mc_attempts = (int64_t)h[6];
+        stats->base_cases = total_base;
+        stats->mc_samples = (int64_t)h[8];
+        stats->levels = levels_seen;
+        stats->ms_build = tm.ms(0, 1);
+        stats->ms_traverse = tm.ms(2, 3) - base_ms;
+        stats->ms_base = base_ms;
+        stats->ms_finalize = tm.ms(4, 5);
+        stats->base_triples = (int64_t)h[12];
+    }
+    if (cfg.validate) return mbm_check_flags(ctx, s);
+    return MBM_OK;
 }

@@ -143,3 +143,15 @@ def test_repeat_calls_stable():
     a = _gpu(X, "fp32")
     b = _gpu(X, "fp32")
     assert _rel(a, b) <= 1e-12
+
+
+def test_sampled_exact_matches_oracle():
+    """The sampled exact kernel (reference for tree accuracy at large N)."""
+    X = inputs.uniform_cube(3000, 14.4, 0.5, 57)
+    idx = inputs.sample_indices(len(X), 40, 3)
+    got = api.potential_sampled(torch.from_numpy(X).cuda(), idx).cpu().numpy()
+    ref, ref_abs = oracle.phi(X, idx, with_abs=True)
+    assert np.all(np.abs(got - ref) <= TOL["fp32"] * ref_abs)
+    # agrees with the full exhaustive FP32 solve on the same particles
+    full = _gpu(X, "fp32")[idx]
+    assert np.all(np.abs(got - full) <= TOL["fp32"] * ref_abs)

@@ -99,7 +99,7 @@ def test_eps_zero_is_exact_and_counts_partition(gmm):
 @pytest.mark.parametrize("eps,alpha", [(0.1, 0.0), (0.01, 0.0), (0.1, 0.05), (0.01, 0.05)])
 def test_guarantees_and_partition(gmm, eps, alpha):
     X, ex = gmm
-    phi, cnt, st = tree.tree_potential(X, eps=eps, alpha=alpha, with_counts=True)
+    phi, cnt, st = tree.tree_potential(X, eps=eps, alpha=alpha, zeta=4.0, with_counts=True)
     assert np.all(cnt == comb(len(X) - 1, 2))
     assert st["det_prunes"] + st["mc_prunes"] > 0
     within = np.abs(phi - ex) <= eps * np.abs(ex)
@@ -122,8 +122,8 @@ def test_absolute_rule(gmm):
 
 def test_mc_is_deterministic_in_seed(gmm):
     X, _ = gmm
-    a, _, sa = tree.tree_potential(X, eps=0.1, alpha=0.05, seed=7)
-    b, _, sb = tree.tree_potential(X, eps=0.1, alpha=0.05, seed=7)
-    c, _, sc = tree.tree_potential(X, eps=0.1, alpha=0.05, seed=8)
+    a, _, sa = tree.tree_potential(X, eps=0.1, alpha=0.05, seed=7, zeta=4.0)
+    b, _, sb = tree.tree_potential(X, eps=0.1, alpha=0.05, seed=7, zeta=4.0)
+    c, _, sc = tree.tree_potential(X, eps=0.1, alpha=0.05, seed=8, zeta=4.0)
     assert np.array_equal(a, b) and sa == sb
     assert sc["mc_samples"] != sa["mc_samples"] or not np.array_equal(a, c)
