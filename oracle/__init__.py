@@ -57,8 +57,8 @@ def lib():
             L.oracle_at_phi.argtypes = [dp, dp, dp]
             L.oracle_phi.argtypes = [dp, i64, ip, i64, dp, dp, ctypes.c_int]
             L.oracle_energy.argtypes = [dp, i64, dp, ctypes.c_int]
-            L.oracle_grad.argtypes = [dp, i64, ip, i64, dp, ctypes.c_int]
-            L.oracle_vjp.argtypes = [dp, i64, dp, ip, i64, dp, ctypes.c_int]
+            L.oracle_grad.argtypes = [dp, i64, ip, i64, dp, dp, ctypes.c_int]
+            L.oracle_vjp.argtypes = [dp, i64, dp, ip, i64, dp, dp, ctypes.c_int]
             L.oracle_max_threads.restype = ctypes.c_int
             if hasattr(L, "oracle_tree_potential"):
                 _bind_tree(L)
@@ -117,23 +117,27 @@ def energy(X, nthreads=0) -> float:
     return float(out[0])
 
 
-def grad(X, idx=None, nthreads=0):
-    """dE/dx_i for the given indices (forces are the negative)."""
+def grad(X, idx=None, nthreads=0, with_norm=False):
+    """dE/dx_i for the given indices (forces are the negative). with_norm also
+    returns sum over the triples of |grad_i phi| (scale for rounding errors)."""
     X = _points(X)
     n = len(X)
     idx = np.arange(n, dtype=np.int64) if idx is None else np.ascontiguousarray(idx, dtype=np.int64)
     out = np.zeros((len(idx), 3))
-    rc = lib().oracle_grad(_dp(X), n, _ip(idx), len(idx), _dp(out), int(nthreads))
+    nrm = np.zeros(len(idx)) if with_norm else None
+    rc = lib().oracle_grad(_dp(X), n, _ip(idx), len(idx), _dp(out),
+                           _dp(nrm) if with_norm else None, int(nthreads))
     if rc != 0:
         raise RuntimeError(f"oracle_grad failed ({rc})")
-    return out
+    return (out, nrm) if with_norm else out
 
 
-def forces(X, idx=None, nthreads=0):
-    return -grad(X, idx, nthreads)
+def forces(X, idx=None, nthreads=0, with_norm=False):
+    r = grad(X, idx, nthreads, with_norm)
+    return (-r[0], r[1]) if with_norm else -r
 
 
-def vjp(X, g, idx=None, nthreads=0):
+def vjp(X, g, idx=None, nthreads=0, with_norm=False):
     """d/dx_m of sum_l g_l Phi_l for the given indices m."""
     X = _points(X)
     n = len(X)
@@ -142,10 +146,12 @@ def vjp(X, g, idx=None, nthreads=0):
         raise ValueError("g must have shape (N,)")
     idx = np.arange(n, dtype=np.int64) if idx is None else np.ascontiguousarray(idx, dtype=np.int64)
     out = np.zeros((len(idx), 3))
-    rc = lib().oracle_vjp(_dp(X), n, _dp(g), _ip(idx), len(idx), _dp(out), int(nthreads))
+    nrm = np.zeros(len(idx)) if with_norm else None
+    rc = lib().oracle_vjp(_dp(X), n, _dp(g), _ip(idx), len(idx), _dp(out),
+                          _dp(nrm) if with_norm else None, int(nthreads))
     if rc != 0:
         raise RuntimeError(f"oracle_vjp failed ({rc})")
-    return out
+    return (out, nrm) if with_norm else out
 
 
 def _bind_tree(L):  # filled in by the tree oracle bindings

@@ -159,14 +159,14 @@ static void at_grad_first(const double* xi, const double* xj, const double* xk,
 
 /* Gradient of E with respect to x_i for each requested i (forces are -grad). */
 int oracle_grad(const double* X, int64_t N, const int64_t* idx, int64_t n_idx,
-                double* out3, int nthreads) {
+                double* out3, double* normout, int nthreads) {
     if (N < 0 || n_idx < 0) return -1;
     int nt = nthreads_or_default(nthreads);
     int64_t q;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
     for (q = 0; q < n_idx; ++q) {
         int64_t i = idx[q];
-        nsum_t acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+        nsum_t acc[3] = {{0, 0}, {0, 0}, {0, 0}}, nrm = {0, 0};
         for (int64_t j = 0; j < N; ++j) {
             if (j == i) continue;
             for (int64_t k = j + 1; k < N; ++k) {
@@ -174,9 +174,11 @@ int oracle_grad(const double* X, int64_t N, const int64_t* idx, int64_t n_idx,
                 double g[3];
                 at_grad_first(X + 3 * i, X + 3 * j, X + 3 * k, g, NULL);
                 for (int d = 0; d < 3; ++d) nsum_add(&acc[d], g[d]);
+                if (normout) nsum_add(&nrm, sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
             }
         }
         for (int d = 0; d < 3; ++d) out3[3 * q + d] = nsum_get(&acc[d]);
+        if (normout) normout[q] = nsum_get(&nrm);
     }
     return 0;
 }
@@ -185,14 +187,14 @@ int oracle_grad(const double* X, int64_t N, const int64_t* idx, int64_t n_idx,
  * sum_l g_l Phi_l = sum_{a<b<c} (g_a + g_b + g_c) phi_abc, so
  * out_m = sum_{j<k; j,k != m} (g_m + g_j + g_k) d phi(x_m,x_j,x_k)/d x_m. */
 int oracle_vjp(const double* X, int64_t N, const double* gw, const int64_t* idx,
-               int64_t n_idx, double* out3, int nthreads) {
+               int64_t n_idx, double* out3, double* normout, int nthreads) {
     if (N < 0 || n_idx < 0) return -1;
     int nt = nthreads_or_default(nthreads);
     int64_t q;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
     for (q = 0; q < n_idx; ++q) {
         int64_t m = idx[q];
-        nsum_t acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+        nsum_t acc[3] = {{0, 0}, {0, 0}, {0, 0}}, nrm = {0, 0};
         for (int64_t j = 0; j < N; ++j) {
             if (j == m) continue;
             for (int64_t k = j + 1; k < N; ++k) {
@@ -201,9 +203,11 @@ int oracle_vjp(const double* X, int64_t N, const double* gw, const int64_t* idx,
                 at_grad_first(X + 3 * m, X + 3 * j, X + 3 * k, g, NULL);
                 double wgt = gw[m] + gw[j] + gw[k];
                 for (int d = 0; d < 3; ++d) nsum_add(&acc[d], wgt * g[d]);
+                if (normout) nsum_add(&nrm, fabs(wgt) * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
             }
         }
         for (int d = 0; d < 3; ++d) out3[3 * q + d] = nsum_get(&acc[d]);
+        if (normout) normout[q] = nsum_get(&nrm);
     }
     return 0;
 }
