@@ -233,6 +233,63 @@ mbm_status mbm_potential_vjp(mbm_ctx* ctx, const double* X_dev, int64_t N, const
 mbm_status mbm_potential_fp32_noalloc(const double* X_dev, int64_t N, double* phi_dev,
                                       mbm_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Serving (no counterpart in the paper): continuous batching of potential
+ * and force requests of uneven N on one GPU. Each of `slots` workers owns a
+ * context and a non-blocking stream; a request starts as soon as a slot is
+ * free and its estimated device footprint fits the budget (oldest first, with
+ * backfill of younger requests that fit beside the room held for the oldest),
+ * so requests overlap on the device. A non-zero system_id keeps that point
+ * set (and its tree, for tree solves) resident until evicted (least recently
+ * used, when the budget needs the room); a system id names a fixed point set.
+ * ------------------------------------------------------------------------ */
+typedef struct mbm_server mbm_server;
+
+enum { MBM_REQ_POTENTIAL = 0, MBM_REQ_FORCES = 1 };
+
+typedef struct {
+    int32_t kind;          /* MBM_REQ_POTENTIAL or MBM_REQ_FORCES */
+    int32_t mode;          /* MBM_EXH_FP32 / MBM_EXH_FP64 / MBM_TREE[|MBM_ABS] (tree: potential) */
+    int64_t N;
+    const double* X_host;  /* N x 3 FP64, caller-owned, read while the request runs */
+    double* out_host;      /* N (potential) or N x 3 (forces) FP64, caller-owned, written */
+    double eps, alpha;     /* tree modes (as in mbm_potential) */
+    uint64_t system_id;    /* != 0: keep / reuse this point set on the device */
+    const mbm_config* cfg; /* NULL = defaults; copied by mbm_submit */
+} mbm_request;
+
+typedef struct {
+    int32_t status;        /* status of the solve */
+    int32_t slot;          /* worker that ran it */
+    double queue_ms;       /* submit -> start */
+    double compute_ms;     /* start -> result in out_host */
+    double latency_ms;     /* submit -> result in out_host */
+    int64_t bytes_reserved;/* footprint estimate admitted against the budget */
+} mbm_result;
+
+/* Create a server on `device` with `slots` (1..64) workers and an HBM budget
+ * (0 = none). Buffers and contexts are owned by the server. */
+mbm_status mbm_server_create(int device, size_t hbm_budget_bytes, int32_t slots,
+                             mbm_server** out);
+
+/* Stop the workers (requests not yet started are dropped) and free everything. */
+mbm_status mbm_server_destroy(mbm_server* server);
+
+/* Queue a request; *ticket identifies it. The request struct is copied; the
+ * caller keeps X_host and out_host alive until mbm_poll reports completion.
+ * MBM_EBUDGET if its estimated footprint alone exceeds the budget. */
+mbm_status mbm_submit(mbm_server* server, const mbm_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_us (0 = do not wait, < 0 = forever) for a ticket.
+ * Returns MBM_OK with *res filled (res->status is the solve's status),
+ * MBM_PENDING (timeout_us = 0, not finished), MBM_ETIMEDOUT, or MBM_EINVAL
+ * for an unknown or already collected ticket. */
+mbm_status mbm_poll(mbm_server* server, uint64_t ticket, mbm_result* res, int64_t timeout_us);
+
+/* Counters: requests admitted, waiting, rejected, completed; bytes held. */
+mbm_status mbm_server_stats(mbm_server* server, int64_t* admitted, int64_t* pending,
+                            int64_t* rejected, int64_t* completed, size_t* reserved);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,6 +53,24 @@ _lock = threading.Lock()
 
 _vp, _i64, _dbl, _int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
 
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("mode", ctypes.c_int32), ("N", ctypes.c_int64),
+                ("X_host", ctypes.c_void_p), ("out_host", ctypes.c_void_p),
+                ("eps", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("system_id", ctypes.c_uint64), ("cfg", ctypes.POINTER(Config))]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32),
+                ("queue_ms", ctypes.c_double), ("compute_ms", ctypes.c_double),
+                ("latency_ms", ctypes.c_double), ("bytes_reserved", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+MBM_REQ_POTENTIAL, MBM_REQ_FORCES = 0, 1
+
 # name -> (restype, argtypes); mirrors include/mbm.h
 SIGNATURES = {
     "mbm_version": (ctypes.c_char_p, []),
@@ -77,6 +95,13 @@ SIGNATURES = {
                              ctypes.POINTER(ctypes.c_int32)]),
     "mbm_tree_export": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mbm_potential_sampled": (_int, [_vp, _vp, _i64, _vp, _i64, _vp, _vp]),
+    "mbm_server_create": (_int, [_int, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(_vp)]),
+    "mbm_server_destroy": (_int, [_vp]),
+    "mbm_submit": (_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "mbm_poll": (_int, [_vp, ctypes.c_uint64, ctypes.POINTER(Result), _i64]),
+    "mbm_server_stats": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                ctypes.POINTER(ctypes.c_size_t)]),
 }
 OPTIONAL = {}
 

@@ -249,3 +249,62 @@ class Potential(torch.autograd.Function):
     def backward(ctx, grad_phi):
         (X,) = ctx.saved_tensors
         return potential_vjp(X.detach(), grad_phi, mode=ctx.mode).to(X.dtype), None
+
+
+class Server:
+    """Continuous-batching request server (mbm_server) on one GPU.
+
+    submit() takes host numpy arrays and returns a ticket; poll() waits for
+    it. Results land in the numpy output the request was given."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, slots: int = 4):
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().mbm_server_create(int(device), int(hbm_budget_bytes), int(slots),
+                                                 ctypes.byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, X: np.ndarray, kind: str = "potential", mode="fp32", eps: float = 0.0,
+               alpha: float = 0.0, system_id: int = 0, config: _lib.Config | None = None,
+               out: np.ndarray | None = None) -> int:
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        n = X.shape[0]
+        k = _lib.MBM_REQ_FORCES if kind == "forces" else _lib.MBM_REQ_POTENTIAL
+        if out is None:
+            out = np.empty((n, 3) if k == _lib.MBM_REQ_FORCES else n, dtype=np.float64)
+        cfg = config if config is not None else _lib.default_config()
+        req = _lib.Request(k, _mode(mode), n, X.ctypes.data, out.ctypes.data, float(eps),
+                           float(alpha), int(system_id), ctypes.pointer(cfg))
+        t = ctypes.c_uint64()
+        _lib.check(_lib.load().mbm_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = (X, out, cfg)
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = -1):
+        """(status, result dict, output array); status MBM_PENDING / MBM_ETIMEDOUT when not done."""
+        r = _lib.Result()
+        st = _lib.load().mbm_poll(self.handle, int(ticket), ctypes.byref(r), int(timeout_us))
+        if st in (_lib.MBM_PENDING, -5):
+            return st, None, None
+        _lib.check(st)
+        X, out, _ = self._keep.pop(ticket)
+        return r.status, r.as_dict(), out
+
+    def stats(self):
+        a, p, r, c = (ctypes.c_int64() for _ in range(4))
+        b = ctypes.c_size_t()
+        _lib.check(_lib.load().mbm_server_stats(self.handle, ctypes.byref(a), ctypes.byref(p),
+                                                ctypes.byref(r), ctypes.byref(c), ctypes.byref(b)))
+        return {"admitted": a.value, "pending": p.value, "rejected": r.value,
+                "completed": c.value, "reserved_bytes": b.value}
+
+    def close(self):
+        if self.handle:
+            _lib.load().mbm_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
