@@ -5,26 +5,32 @@ Headline step: one exhaustive FP32-bulk solve of Phi for the N = 32 768
 uniform workload (cube of side 32, minimum pair distance 0.5, seed 2), i.e.
 all C(N,3) = 5.8635e12 unordered triples. The metric is triples/s.
 
-The JSON line also carries, for context: the FP64 exhaustive rate,
-the multi-tree particles/s at eps = 1e-2 on the 2^20-point Gaussian mixture
-(when built), the roofline of the dominant kernel, the CPU oracle baseline,
-an end-to-end number through the host-buffer C entry point, and the SM
-clocks sampled during the timed region.
+The JSON line also carries, for context (each time-bounded):
+  fp64_exhaustive : plain FP64 exhaustive rate (N = 8 192, same density);
+  tree            : multi-tree particles/s at eps = 1e-2 and 1e-1, alpha = 0.05,
+                    on 65 536 points from the 2^20 Gaussian-mixture generator
+                    (4 components of 16 384 points at the same component
+                    density); % within eps on sampled particles against the
+                    exact sum; speedup over plain FP64 exhaustive particles/s;
+  forces          : adjoint (force) rate at N = 16 384, force-workload density;
+  serving         : Poisson stream of the serving mix (potential 70 % / forces
+                    30 %, uniform and Gaussian-mixture systems) with p50/p99;
+plus the roofline of the dominant kernel, the CPU oracle baseline, an
+end-to-end number through the host-buffer C entry point, and the SM clocks
+sampled during the timed region.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun each rank runs an independent replica (the exhaustive sum
-needs no exchange for one system); value = all ranks' triples / max time.
+Under torchrun each rank runs an independent replica (the exhaustive sum of
+one system needs no exchange); value = all ranks' triples / max time.
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -35,6 +41,7 @@ WORKLOAD = "exh32_n32768"
 N_MAIN = 32768
 FLOPS_PER_TRIPLE_FP32 = 25   # counted from the inner loop (FMA = 2), see csrc/tile_fp32.cuh
 FP32_LANES_PER_SM = 128
+N_CONFIG3 = 1 << 20
 
 
 def triples(n):
@@ -42,12 +49,27 @@ def triples(n):
 
 
 def _peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
-        with open(path) as f:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
     except Exception:
         return {}
+
+
+def aggregate(local_ms: float, units: float, dist=None):
+    """Whole-job rate over ranks: units of all ranks / max time (weak scaling).
+    Returns (value, max_ms); with dist None or world size 1 it is local."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return units / (local_ms / 1e3), local_ms
+    import torch
+    t = torch.tensor([local_ms, units], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t = t.cuda()
+    m = t.clone()
+    dist.all_reduce(m[0:1], op=dist.ReduceOp.MAX)
+    dist.all_reduce(m[1:2], op=dist.ReduceOp.SUM)
+    max_ms, tot = float(m[0]), float(m[1])
+    return tot / (max_ms / 1e3), max_ms
 
 
 class ClockSampler:
@@ -123,18 +145,15 @@ def cpu_oracle_rate(X, n_particles, seed=2024):
 
 def run_reference(args):
     """The oracle as it stands, timed on the host cores (rank 0 only)."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return 0
     from paper_1105_2769_gb300 import inputs
     X = inputs.workload(WORKLOAD)
     import oracle
     oracle.build()
     nt = oracle.max_threads()
-    rates = []
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        cpu_oracle_rate(X, nt)
-    total_t = 0.0
+    cpu_oracle_rate(X, nt)  # warm-up (page-in, thread start)
+    rates, total_t = [], 0.0
     for _ in range(args.steps):
         r, dt, m, nt = cpu_oracle_rate(X, nt)
         rates.append(r)
@@ -142,19 +161,124 @@ def run_reference(args):
     value = sum(rates) / len(rates)
     sample = (f"{nt} seeded particles per step of the N={N_MAIN} set (each a full "
               f"C(N-1,2) sum); job-equivalent triples = evaluations/3")
-    line = {
+    print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "triples/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N_MAIN, "distribution": "uniform [0,32]^3, d_min 0.5, seed 2"},
+        "config": {"workload": WORKLOAD, "n": N_MAIN,
+                   "distribution": "uniform [0,32]^3, d_min 0.5, seed 2"},
         "cpu_baseline": {"value": value, "unit": "triples/s", "cores": nt, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "triples/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line))
+    }))
     return 0
+
+
+def bench_fp64(api, inputs, torch, dev):
+    n64 = 8192
+    X = inputs.uniform_cube(n64, 32.0 * (n64 / N_MAIN) ** (1 / 3), 0.5, 2)
+    Xd = torch.from_numpy(X).to(dev)
+    api.potential(Xd, mode="fp64")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.potential(Xd, mode="fp64")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"n": n64, "triples_per_s": triples(n64) / dt, "s": dt}
+
+
+def bench_tree(api, inputs, torch, dev, r64, np):
+    X = inputs.workload("gmm4_n65536")
+    n = len(X)
+    Xd = torch.from_numpy(X).to(dev)
+    idx = inputs.sample_indices(n, 32, 11)
+    exact = api.potential_sampled(Xd, idx).cpu().numpy()
+    out = {"workload": "gmm4_n65536", "n": n, "alpha": 0.05, "sampled_particles": len(idx)}
+    fp64_pps = n * r64 / triples(n)                       # plain FP64 exhaustive particles/s
+    fp64_pps_config3 = N_CONFIG3 * r64 / triples(N_CONFIG3)
+    for eps in (1e-2, 1e-1):
+        api.potential(Xd, eps=eps, alpha=0.05, mode="tree")  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        phi, st = api.potential(Xd, eps=eps, alpha=0.05, mode="tree", stats=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        rel = np.abs(phi.cpu().numpy()[idx] - exact) / np.abs(exact)
+        out[f"eps_{eps:g}"] = {
+            "particles_per_s": n / dt, "s": dt, "within_eps": float(np.mean(rel <= eps)),
+            "max_rel_err": float(rel.max()), "speedup_vs_fp64_exhaustive": n / dt / fp64_pps,
+            "phase_ms": {k: round(st[k], 2) for k in
+                         ("ms_build", "ms_traverse", "ms_base", "ms_finalize")},
+            "det_prunes": st["det_prunes"], "mc_prunes": st["mc_prunes"],
+            "base_triples": st["base_triples"], "mc_samples": st["mc_samples"]}
+    out["fp64_exhaustive_particles_per_s"] = fp64_pps
+    out["fp64_exhaustive_particles_per_s_n1048576"] = fp64_pps_config3
+    return out
+
+
+def bench_forces(api, inputs, torch, dev):
+    n = 16384
+    X = inputs.uniform_cube(n, 32.0 * (n / 65536) ** (1 / 3), 0.5, 4)
+    Xd = torch.from_numpy(X).to(dev)
+    api.forces(Xd, mode="fp32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    api.forces(Xd, mode="fp32")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"n": n, "triples_per_s": triples(n) / dt, "s": dt,
+            "note": "gather form: each unordered triple evaluated once per member"}
+
+
+def bench_serving(api, inputs, np, duration=6.0, rate=200.0):
+    """Poisson arrivals of the serving mix with N log-uniform in [1 024, 4 096]."""
+    rng = np.random.default_rng(5)
+    systems = []
+    for q in range(24):
+        n = int(np.exp(rng.uniform(np.log(1024), np.log(4096))))
+        if q % 2:
+            X = inputs.uniform_cube(n, n ** (1 / 3), 0.5, 500 + q)
+        else:
+            X = inputs.gaussian_mixture(n, max(1, n // 16384 + 1), 100.0 * (n / N_CONFIG3) ** (1 / 3),
+                                        0.5, 3.0, 0.05, 500 + q)
+        systems.append(X)
+    srv = api.Server(0, hbm_budget_bytes=120 << 30, slots=8)
+    # warm the slots
+    for X in systems[:8]:
+        srv.poll(srv.submit(X, mode="fp32"))
+    n_req = int(duration * rate)
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    kinds = rng.uniform(size=n_req) < 0.7
+    picks = rng.integers(0, len(systems), size=n_req)
+    tickets, parts = [], 0
+    t_start = time.perf_counter()
+    t_next = t_start
+    for q in range(n_req):
+        t_next += gaps[q]
+        while time.perf_counter() < t_next:
+            time.sleep(0.0002)
+        X = systems[picks[q]]
+        parts += len(X)
+        if kinds[q]:
+            tickets.append(srv.submit(X, mode="tree", eps=1e-2, alpha=0.05,
+                                      system_id=int(picks[q]) + 1))
+        else:
+            tickets.append(srv.submit(X, kind="forces", mode="fp32"))
+    lat = []
+    for t in tickets:
+        st, res, _ = srv.poll(t)
+        lat.append(res["latency_ms"])
+    wall = time.perf_counter() - t_start
+    stats = srv.stats()
+    srv.close()
+    return {"offered_req_per_s": rate, "requests": n_req, "served_req_per_s": n_req / wall,
+            "particles_per_s": parts / wall, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall, "slots": 8,
+            "n_range": [1024, 4096], "admitted": stats["admitted"],
+            "rejected": stats["rejected"],
+            "mix": "70% tree Phi (eps 1e-2, alpha 0.05, resident systems), 30% FP32 forces"}
 
 
 def main():
@@ -164,7 +288,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip FP64/tree/serving context")
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64/tree/forces/serving")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -214,26 +338,21 @@ def main():
     clocks = sampler.stop()
     if world > 1:
         dist.barrier()
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     n_trip = triples(len(X))
-    value = world * n_trip * args.steps / (tot_ms / 1e3)
+    value, tot_ms = aggregate(tot_ms, float(n_trip * args.steps), dist if world > 1 else None)
 
-    # roofline of the dominant kernel (FP32 ALU bound)
     props = torch.cuda.get_device_properties(dev)
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sm_max = float(_peaks().get("sm_max_mhz", 2070.0))
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     k_ms = sum(kernel_ms) / len(kernel_ms)
     achieved = FLOPS_PER_TRIPLE_FP32 * n_trip / (k_ms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": None,
-                "peak_note": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
-                "flops_per_triple": FLOPS_PER_TRIPLE_FP32, "kernel_ms": k_ms}
+                "peak_note": (f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 "
+                              f"x {sm_max:.0f} MHz (maximum SM clock)"),
+                "kernel": "exh_fp32_kernel", "flops_per_triple": FLOPS_PER_TRIPLE_FP32,
+                "kernel_ms": k_ms}
     if clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (peak_tflops * clocks["sm_mhz"] / sm_max)
 
@@ -249,22 +368,6 @@ def main():
     e2e = {"value": world * n_trip / e2e_s, "unit": "triples/s",
            "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(ph.nbytes)}
 
-    extras = {}
-    if not args.no_extras and rank == 0:
-        # plain FP64 exhaustive rate on the same distribution (density 1, d_min 0.5)
-        n64 = 8192
-        X64 = inputs.uniform_cube(n64, 32.0 * (n64 / N_MAIN) ** (1 / 3), 0.5, 2)
-        X64d = torch.from_numpy(X64).to(dev)
-        api.potential(X64d, mode="fp64")
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        api.potential(X64d, mode="fp64")
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        r64 = triples(n64) / dt
-        extras["fp64_exhaustive"] = {"n": n64, "triples_per_s": r64,
-                                     "fp32_over_fp64": value / world / r64}
-
     line = {
         "metric": METRIC, "value": value, "unit": "triples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
@@ -279,7 +382,13 @@ def main():
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }
-    line.update(extras)
+    if not args.no_extras and rank == 0:
+        fp64 = bench_fp64(api, inputs, torch, dev)
+        fp64["fp32_over_fp64"] = value / world / fp64["triples_per_s"]
+        line["fp64_exhaustive"] = fp64
+        line["tree"] = bench_tree(api, inputs, torch, dev, fp64["triples_per_s"], np)
+        line["forces"] = bench_forces(api, inputs, torch, dev)
+        line["serving"] = bench_serving(api, inputs, np)
     if rank == 0 and not args.no_cpu_baseline:
         r, dt, m, nt = cpu_oracle_rate(X, 0)
         line["cpu_baseline"] = {"value": r, "unit": "triples/s", "cores": nt, "kind": "oracle",

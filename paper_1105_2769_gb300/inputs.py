@@ -193,6 +193,10 @@ def workload(name: str, return_stats: bool = False):
     gmm_n1048576    : N=2^20, 64-component GMM (centres U[0,100]^3,
                       sigma U[0.5,3]), d_min 0.05, seed 3
     forces_n65536   : N=65 536, U[0,32]^3, d_min 0.5, seed 4
+    gmm4_n65536     : N=65 536 from the same generator as gmm_n1048576 with 4
+                      components (16 384 points each, as there) in a cube of
+                      side 100 (4/64)^(1/3), so component density and
+                      per-component structure match the 2^20 set; seed 3
     """
     if name == "exh64_n512":
         r = uniform_cube(512, 1.0, 0.01, 1, return_stats=True)
@@ -202,6 +206,9 @@ def workload(name: str, return_stats: bool = False):
         r = gaussian_mixture(1 << 20, 64, 100.0, 0.5, 3.0, 0.05, 3, return_stats=True)
     elif name == "forces_n65536":
         r = uniform_cube(65536, 32.0, 0.5, 4, return_stats=True)
+    elif name == "gmm4_n65536":
+        r = gaussian_mixture(65536, 4, 100.0 * (4 / 64) ** (1 / 3), 0.5, 3.0, 0.05, 3,
+                             return_stats=True)
     else:
         raise KeyError(name)
     return r if return_stats else r[0]
