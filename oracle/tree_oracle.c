@@ -337,27 +337,33 @@ static int mc_point(osolve* S, const int64_t P[3], int slot, int64_t x, double T
     const otree* t = S->t;
     double mean = 0.0, m2 = 0.0;
     int m = 0, pass = 0;
+    uint32_t r[4] = {0, 0, 0, 0};
     for (;;) {
-        uint32_t ctr[4] = {(uint32_t)x, (uint32_t)P[0] | ((uint32_t)(m & 0xFF) << 24),
-                           (uint32_t)P[1] | ((uint32_t)((m >> 8) & 0xFF) << 24), (uint32_t)P[2]};
-        uint32_t r[4];
-        oracle_philox4x32_10(ctr, S->key, r);
+        /* one Philox call per two samples: sample m uses words 2(m%2), 2(m%2)+1
+           of the call with counter index m/2 */
+        if ((m & 1) == 0) {
+            int c = m >> 1;
+            uint32_t ctr[4] = {(uint32_t)x, (uint32_t)P[0] | ((uint32_t)(c & 0xFF) << 24),
+                               (uint32_t)P[1] | ((uint32_t)((c >> 8) & 0xFF) << 24), (uint32_t)P[2]};
+            oracle_philox4x32_10(ctr, S->key, r);
+        }
         int64_t y, z;
-        draw_partners(S, P, slot, x, r[0], r[1], &y, &z);
+        draw_partners(S, P, slot, x, (m & 1) ? r[2] : r[0], (m & 1) ? r[3] : r[1], &y, &z);
         double f = oracle_at_phi(t->Xs + 3 * x, t->Xs + 3 * y, t->Xs + 3 * z);
         ++m;
         double dlt = f - mean;
-        mean += dlt / m;
-        m2 += dlt * (f - mean);
+        mean += dlt * (1.0 / (double)m);                 /* running mean */
+        m2 += dlt * (f - mean);                          /* running sum of squares */
         if (m >= 2 && (m >= 30 || m >= S->m_limit)) { /* the loop can only end here */
-            double sig = sqrt(m2 / (m - 1)) / sqrt((double)m);
+            /* sigma_mu = s / sqrt(m), s^2 = m2 / (m - 1) (sample variance with m-1) */
+            double sig = sqrt(m2 * (1.0 / (double)(m - 1)) * (1.0 / (double)m));
             double lhs = S->z * sig, rhs;
             double lb = phil - Ti * (fabs(mean) + S->z * sig);
             if (lb < 0.0) lb = 0.0;
             if (S->mc_rule == 1) /* as printed: T_i z sigma <= (eps lb + tau T_i) / T^root */
-                rhs = (S->eps * lb / Ti + S->tau) / S->troot;
+                rhs = (S->eps * lb / Ti + S->tau) * (1.0 / S->troot);
             else                 /* T_i on both terms */
-                rhs = (S->eps * lb + S->tau) / S->troot;
+                rhs = (S->eps * lb + S->tau) * (1.0 / S->troot);
             pass = lhs <= rhs;
             if ((pass && m >= 30) || m >= S->m_limit) break;
         } else if (m >= S->m_limit) {

@@ -126,7 +126,7 @@ __device__ __forceinline__ float tile_triples(const TabPair (*tab)[kTile / 2], c
             acc[p] = make_float2(0.f, 0.f);
         }
         const float2 m3 = f2_splat(-3.0f), one = f2_splat(1.0f);
-#pragma unroll 1
+#pragma unroll 2
         for (int jj = 0; jj < kTile; ++jj) {
             float s;
             const PairF pu = pair_unit(ih, il, sJh[jj], sJl[jj], &s);

@@ -420,6 +420,8 @@ struct Trav {
     const double* xs;
     const float4 *xh, *xl;
     double eps, tau, troot, zeta, z, alpha;
+    double inv_troot;          // 1 / T^root
+    const double* rcp;         // rcp[m] = 1/m (correctly rounded), m = 1..m_limit
     int m_limit, mc_rule;
     uint32_t key0, key1;
     double* node_acc;
@@ -757,14 +759,31 @@ __device__ void draw_partners(const int64_t P[3], const int64_t bb[3], const int
     }
 }
 
+// Unit vector and r^-3 of one pair for Monte Carlo samples: one Newton step
+// on rsqrt, rho = y^3 (a few ulp; a sample's rounding is far below the
+// sampling error it feeds).
+__device__ __forceinline__ mbm_tile::PairF pair_sample(float4 ph, float4 pl, float4 qh, float4 ql) {
+    const float dx = (qh.x - ph.x) + (ql.x - pl.x);
+    const float dy = (qh.y - ph.y) + (ql.y - pl.y);
+    const float dz = (qh.z - ph.z) + (ql.z - pl.z);
+    const float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    float y = rsqrtf(s);
+    y = fmaf(0.5f * y, fmaf(-s * y, y, 1.0f), y);
+    mbm_tile::PairF r;
+    r.ex = dx * y;
+    r.ey = dy * y;
+    r.ez = dz * y;
+    r.rho = y * y * y;
+    return r;
+}
+
 // phi of one point triple in FP32 bulk (direction-cosine form).
 __device__ __forceinline__ float phi_fp32(const float4* xh, const float4* xl, int64_t a, int64_t b,
                                           int64_t c) {
-    float s;
     const float4 ah = xh[a], al = xl[a], bh = xh[b], bl = xl[b], ch = xh[c], cl = xl[c];
-    const mbm_tile::PairF ab = mbm_tile::pair_unit(ah, al, bh, bl, &s);
-    const mbm_tile::PairF ac = mbm_tile::pair_unit(ah, al, ch, cl, &s);
-    const mbm_tile::PairF bc = mbm_tile::pair_unit(bh, bl, ch, cl, &s);
+    const mbm_tile::PairF ab = pair_sample(ah, al, bh, bl);
+    const mbm_tile::PairF ac = pair_sample(ah, al, ch, cl);
+    const mbm_tile::PairF bc = pair_sample(bh, bl, ch, cl);
     const float p1 = ab.ex * ac.ex + ab.ey * ac.ey + ab.ez * ac.ez;
     const float p2 = ab.ex * bc.ex + ab.ey * bc.ey + ab.ez * bc.ez;
     const float p3 = ac.ex * bc.ex + ac.ey * bc.ey + ac.ez * bc.ez;
@@ -804,30 +823,35 @@ __device__ double mc_warp(const Trav& p, const int64_t P[3], const int64_t bb[3]
     int m = 0;
     bool pass = false, done = !active;
     int samples = 0, iter = 0;
+    uint32_t rr[4] = {0, 0, 0, 0};
     while (__any_sync(0xffffffffu, !done)) {
         if (!done) {
-            const uint32_t ctr1 = (uint32_t)P[0] | ((uint32_t)(m & 0xFF) << 24);
-            const uint32_t ctr2 = (uint32_t)P[1] | ((uint32_t)((m >> 8) & 0xFF) << 24);
-            uint32_t r[4];
-            philox4x32_10((uint32_t)x, ctr1, ctr2, (uint32_t)P[2], p.key0, p.key1, r);
+            // one Philox call serves samples 2c and 2c+1 (words 0,1 and 2,3)
+            if ((m & 1) == 0) {
+                const int c = m >> 1;
+                const uint32_t ctr1 = (uint32_t)P[0] | ((uint32_t)(c & 0xFF) << 24);
+                const uint32_t ctr2 = (uint32_t)P[1] | ((uint32_t)((c >> 8) & 0xFF) << 24);
+                philox4x32_10((uint32_t)x, ctr1, ctr2, (uint32_t)P[2], p.key0, p.key1, rr);
+            }
+            const uint32_t ra = (m & 1) ? rr[2] : rr[0], rb = (m & 1) ? rr[3] : rr[1];
             int64_t y, zz;
-            draw_partners(P, bb, nn, slot, x, r[0], r[1], y, zz);
+            draw_partners(P, bb, nn, slot, x, ra, rb, y, zz);
             const double f = (double)phi_fp32(p.xh, p.xl, x, y, zz);
             ++m;
             ++samples;
             const double dlt = __dsub_rn(f, mean);
-            mean = __dadd_rn(mean, __ddiv_rn(dlt, (double)m));
+            mean = __dadd_rn(mean, __dmul_rn(dlt, p.rcp[m]));
             m2 = __dadd_rn(m2, __dmul_rn(dlt, __dsub_rn(f, mean)));
             if (m >= 2 && (m >= 30 || m >= p.m_limit)) {  // the test can end the loop only here
-                const double sig =
-                    __ddiv_rn(__dsqrt_rn(__ddiv_rn(m2, (double)(m - 1))), __dsqrt_rn((double)m));
+                // sigma_mu = sqrt(m2 / (m-1) / m), with exact reciprocals
+                const double sig = __dsqrt_rn(__dmul_rn(__dmul_rn(m2, p.rcp[m - 1]), p.rcp[m]));
                 const double lhs = __dmul_rn(p.z, sig);
                 double lb = __dsub_rn(phil, __dmul_rn(Ti, __dadd_rn(fabs(mean), __dmul_rn(p.z, sig))));
                 if (lb < 0.0) lb = 0.0;
                 const double rhs =
                     p.mc_rule == 1
-                        ? __ddiv_rn(__dadd_rn(__ddiv_rn(__dmul_rn(p.eps, lb), Ti), p.tau), p.troot)
-                        : __ddiv_rn(__dadd_rn(__dmul_rn(p.eps, lb), p.tau), p.troot);
+                        ? __dmul_rn(__dadd_rn(__ddiv_rn(__dmul_rn(p.eps, lb), Ti), p.tau), p.inv_troot)
+                        : __dmul_rn(__dadd_rn(__dmul_rn(p.eps, lb), p.tau), p.inv_troot);
                 pass = lhs <= rhs;
                 if ((pass && m >= 30) || m >= p.m_limit) done = true;
             } else if (m >= p.m_limit) {  // m_limit < 2
@@ -861,25 +885,26 @@ __device__ __forceinline__ void candidate_geometry(const Trav& p, const int64_t 
     }
 }
 
-// Probe: each distinct node's particles with the smallest Phi^l(x) first
-// (the likeliest to fail); a warp per (candidate, slot).
+// Probe: each distinct node's 8 particles with the smallest Phi^l(x) (the
+// likeliest to fail) run first; lanes 8s..8s+7 take slot s, a warp per
+// candidate. Decisions do not depend on this order.
+constexpr int kProbe = 8;
 __global__ void mc_probe_kernel(const int4* __restrict__ mc, int64_t n_c, int* cand_fail, Trav p) {
     const int lane = threadIdx.x & 31;
-    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (w >= n_c * 3) return;
-    const int64_t c = w / 3;
-    const int slot = (int)(w % 3);
+    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (c >= n_c) return;
     const int4 t = mc[c];
     const int64_t P[3] = {t.x, t.y, t.z};
-    if (slot > 0 && P[slot] == P[slot - 1]) return;
     volatile int* fail = cand_fail + c;
-    if (*fail) return;
     double T[3];
     bool first[3];
     int64_t bb[3], nn[3], U;
     candidate_geometry(p, P, T, first, bb, nn, U);
-    const int x = p.weak[P[slot] * 32 + lane];
-    mc_warp(p, P, bb, nn, x >= 0, slot, x >= 0 ? x : 0, T[slot], fail);
+    const int slot = lane / kProbe;
+    const bool mine = slot < 3 && first[slot];
+    const int x = mine ? p.weak[P[slot] * 32 + (lane % kProbe)] : -1;
+    mc_warp(p, P, bb, nn, x >= 0, slot < 3 ? slot : 0, x >= 0 ? x : 0, slot < 3 ? T[slot] : 0.0,
+            fail);
 }
 
 __global__ void mc_sizes_kernel(const int4* __restrict__ mc, int64_t n_mc, int64_t N,
@@ -1321,7 +1346,8 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         (size_t)max_levels * cap_lvl * 16,                                 // level buffers
         (size_t)cap_mc * 16, (size_t)cap_base * 16,                        // mc, base
         (size_t)(cap_mc + 2) * 8, (size_t)cap_mc * 4,                      // chunk_off, fail
-        (size_t)cap_est * 8, 256, cub_bytes};                              // est, counters
+        (size_t)cap_est * 8, 256, cub_bytes,                               // est, counters
+        (size_t)(cfg.m_limit + 1) * 8};                                    // 1/m table
     MBM_TRY(mbm_scratch_reserve(ctx, carve_size(parts)));
     Carve sc{static_cast<char*>(ctx->scratch)};
     double* pt_acc = sc.take<double>(N);
@@ -1336,7 +1362,15 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
     double* est = sc.take<double>(cap_est);
     ull* ctr = sc.take<ull>(32);  // 0 n_next, 1 n_mc, 2 n_base, 3.. statistics
     void* cub_tmp = sc.take<char>(cub_bytes);
+    double* rcp = sc.take<double>(cfg.m_limit + 1);
     ull* h = reinterpret_cast<ull*>(ctx->h_flags) + 8;  // pinned, after the status word
+    {
+        std::vector<double> r(cfg.m_limit + 1, 0.0);
+        for (int m = 1; m <= cfg.m_limit; ++m) r[m] = 1.0 / (double)m;
+        MBM_CUDA_TRY(cudaMemcpyAsync(rcp, r.data(), r.size() * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
+        MBM_CUDA_TRY(cudaStreamSynchronize(s));
+    }
 
     MBM_CUDA_TRY(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
     MBM_CUDA_TRY(cudaMemsetAsync(pt_acc, 0, (size_t)N * 8, s));
@@ -1366,6 +1400,8 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
     p.eps = absolute ? 0.0 : eps;
     p.tau = absolute ? eps : cfg.tau;
     p.troot = (double)(N - 1) * (double)(N - 2) * 0.5;
+    p.inv_troot = 1.0 / p.troot;
+    p.rcp = rcp;
     p.zeta = cfg.zeta;
     p.z = z;
     p.alpha = alpha;
@@ -1446,7 +1482,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         const int64_t n_mc = (int64_t)h[1];
         if (n_mc > 0) {
             MBM_CUDA_TRY(cudaMemsetAsync(cand_fail, 0, (size_t)n_mc * sizeof(int), s));
-            mc_probe_kernel<<<grid_of(n_mc * 3 * 32, 256), 256, 0, s>>>(mcl, n_mc, cand_fail, p);
+            mc_probe_kernel<<<grid_of(n_mc * 32, 256), 256, 0, s>>>(mcl, n_mc, cand_fail, p);
             mc_sizes_kernel<<<grid_of(n_mc, 256), 256, 0, s>>>(mcl, n_mc, N, cand_fail, chunk_off);
             MBM_CUDA_TRY(cudaMemsetAsync(chunk_off + n_mc, 0, sizeof(int64_t), s));
             MBM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(cub_tmp, cub_bytes, chunk_off, chunk_off,
