@@ -626,19 +626,25 @@ __global__ void classify_kernel(const int4* __restrict__ front, int64_t n_front,
         box_d2(p, P[0], P[1], sl[0], sh[0]);
         box_d2(p, P[0], P[2], sl[1], sh[1]);
         box_d2(p, P[1], P[2], sl[2], sh[2]);
-        double plo, phi_hi;
-        phi_interval(sl[0], sh[0], sl[1], sh[1], sl[2], sh[2], plo, phi_hi);
-        const double width = __dsub_rn(phi_hi, plo);
-        const double amax = fabs(plo) > fabs(phi_hi) ? fabs(plo) : fabs(phi_hi);
-        double lb = INFINITY;
-        for (int s = 0; s < 3; ++s) {
-            if (!first[s]) continue;
-            const double v = __dsub_rn(p.nphil[P[s]], __dmul_rn(T[s], amax));
-            if (v < lb) lb = v;
+        // Touching boxes (d^l = 0, e.g. a repeated node) leave phi_hi = +inf:
+        // the width is infinite and the rule cannot prune; skip its arithmetic.
+        bool prune = false;
+        if (sl[0] > 0.0 && sl[1] > 0.0 && sl[2] > 0.0) {
+            double plo, phi_hi;
+            phi_interval(sl[0], sh[0], sl[1], sh[1], sl[2], sh[2], plo, phi_hi);
+            const double width = __dsub_rn(phi_hi, plo);
+            const double amax = fabs(plo) > fabs(phi_hi) ? fabs(plo) : fabs(phi_hi);
+            double lb = INFINITY;
+            for (int s = 0; s < 3; ++s) {
+                if (!first[s]) continue;
+                const double v = __dsub_rn(p.nphil[P[s]], __dmul_rn(T[s], amax));
+                if (v < lb) lb = v;
+            }
+            const double budget =
+                __ddiv_rn(__dadd_rn(__dmul_rn(p.eps, lb > 0.0 ? lb : 0.0), p.tau), p.troot);
+            prune = width <= budget;
         }
-        const double budget =
-            __ddiv_rn(__dadd_rn(__dmul_rn(p.eps, lb > 0.0 ? lb : 0.0), p.tau), p.troot);
-        if (width <= budget) {
+        if (prune) {
             act = kActDet;
             const double f = phi_f64(p.ncen + 3 * P[0], p.ncen + 3 * P[1], p.ncen + 3 * P[2]);
             for (int s = 0; s < 3; ++s) {
@@ -819,6 +825,14 @@ __device__ double mc_warp(const Trav& p, const int64_t P[3], const int64_t bb[3]
                           volatile int* fail) {
     const int lane = threadIdx.x & 31;
     const double phil = active ? p.pphil[x] : 0.0;  // the particle's own Phi^l
+    // The bound never exceeds rhs_max = (eps Phi^l(x) + tau)/T^root (rule 0;
+    // rule 1 divides the eps term by T_i), so z^2 sigma^2 > rhs_max^2 (with
+    // slack for rounding) fails the stop test without evaluating it.
+    const double rhs_max = __dmul_rn(
+        __dadd_rn(p.mc_rule == 1 ? __ddiv_rn(__dmul_rn(p.eps, phil), Ti) : __dmul_rn(p.eps, phil),
+                  p.tau),
+        p.inv_troot);
+    const double reject_v = __dmul_rn(__dmul_rn(rhs_max, rhs_max) / (p.z * p.z), 1.0 + 1e-9);
     double mean = 0.0, m2 = 0.0;
     int m = 0;
     bool pass = false, done = !active;
@@ -842,9 +856,14 @@ __device__ double mc_warp(const Trav& p, const int64_t P[3], const int64_t bb[3]
             const double dlt = __dsub_rn(f, mean);
             mean = __dadd_rn(mean, __dmul_rn(dlt, p.rcp[m]));
             m2 = __dadd_rn(m2, __dmul_rn(dlt, __dsub_rn(f, mean)));
-            if (m >= 2 && (m >= 30 || m >= p.m_limit)) {  // the test can end the loop only here
+            const bool testing = m >= 2 && (m >= 30 || m >= p.m_limit);
+            const double var_mu = testing ? __dmul_rn(__dmul_rn(m2, p.rcp[m - 1]), p.rcp[m]) : 0.0;
+            if (testing && var_mu > reject_v) {  // cannot pass at this m
+                pass = false;
+                if (m >= p.m_limit) done = true;
+            } else if (testing) {  // the test can end the loop only here
                 // sigma_mu = sqrt(m2 / (m-1) / m), with exact reciprocals
-                const double sig = __dsqrt_rn(__dmul_rn(__dmul_rn(m2, p.rcp[m - 1]), p.rcp[m]));
+                const double sig = __dsqrt_rn(var_mu);
                 const double lhs = __dmul_rn(p.z, sig);
                 double lb = __dsub_rn(phil, __dmul_rn(Ti, __dadd_rn(fabs(mean), __dmul_rn(p.z, sig))));
                 if (lb < 0.0) lb = 0.0;
