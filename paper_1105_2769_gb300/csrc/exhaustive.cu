@@ -7,8 +7,8 @@
 // three slices Phi(x_a), Phi(x_b), Phi(x_c)).
 //
 // FP32 bulk evaluates each triple in the direction-cosine form (see
-// tile_fp32.cuh: unit edge vectors and r^-3 per pair, 16 FP32 operations and
-// 25 FLOPs per triple). FP64 evaluates the law-of-cosines form on squared
+// tile_fp32.cuh: unit edge vectors and r^-3 per pair, 14 FP32 operations and
+// 23 FLOPs per triple). FP64 evaluates the law-of-cosines form on squared
 // side lengths c = r_ij^2, b = r_ik^2, a = r_jk^2:
 //   cos t_i cos t_j cos t_k = P / (8abc),  P = (b+c-a)(a+c-b)(a+b-c),
 //   phi = (abc + 0.375 P) A B C,  A = a^(-5/2), B = b^(-5/2), C = c^(-5/2).
@@ -286,7 +286,7 @@ struct SampleWarpSmem {
 };
 constexpr int kSampleWarps = 4;
 
-__global__ void __launch_bounds__(kSampleWarps * 32)
+__global__ void __launch_bounds__(kSampleWarps * 32, 1)
 sampled_fp32_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int N, int NT,
                     const int64_t* __restrict__ idx, int n_idx, double* __restrict__ out,
                     long long n_items) {

@@ -11,10 +11,13 @@
 // Loop structure: a lane owns particle i of tile I. (j,k) quantities come from
 // a shared-memory table built once per (J, K); (i,k) quantities are held in
 // registers for one half (16 columns) of K; (i,j) quantities are formed per j.
-// Per pair of triples (packed f32x2): 9 for the three dot products, 2 for
-// p1 p2 p3, 1 for n = 1 - 3t, 1 for rho_ik rho_jk, 1 for the row sum, 1 for
-// the full product, 1 for the column sum: 16 operations per triple, 9 of
-// them FMA -> 25 FLOPs per triple (FMA = 2).
+// With p1' = (-3 e_ij).e_ik (the -3 folded into a per-row copy of e_ij),
+// q = n rho_jk = rho_jk + p1' p2 p3 rho_jk, and
+//   row sum    sum_k phi = rho_ij sum_k q rho_ik,
+//   column sum sum_j phi = rho_ik sum_j q rho_ij,
+// the loop per pair of triples (packed f32x2) is 9 for the dot products, 2 for
+// p1' p2 p3, 1 for q, 1 for the row sum, 1 for the column sum: 14 operations
+// per triple, 9 of them FMA -> 23 FLOPs per triple (FMA = 2).
 #pragma once
 
 #include "device_math.cuh"
@@ -125,15 +128,15 @@ __device__ __forceinline__ float tile_triples(const TabPair (*tab)[kTile / 2], c
             rk[p] = make_float2(e[0][3], e[1][3]);
             acc[p] = make_float2(0.f, 0.f);
         }
-        const float2 m3 = f2_splat(-3.0f), one = f2_splat(1.0f);
 #pragma unroll 2
         for (int jj = 0; jj < kTile; ++jj) {
             float s;
             const PairF pu = pair_unit(ih, il, sJh[jj], sJl[jj], &s);
             const bool v = iv && jj < nJ && (!maskIJ || lane < jj) && s > 0.f;
-            const float2 ux = f2_splat(v ? pu.ex : 0.f);
-            const float2 uy = f2_splat(v ? pu.ey : 0.f);
-            const float2 uz = f2_splat(v ? pu.ez : 0.f);
+            const float ex = v ? pu.ex : 0.f, ey = v ? pu.ey : 0.f, ez = v ? pu.ez : 0.f;
+            const float2 ux = f2_splat(ex), uy = f2_splat(ey), uz = f2_splat(ez);
+            const float2 u3x = f2_splat(-3.0f * ex), u3y = f2_splat(-3.0f * ey),
+                         u3z = f2_splat(-3.0f * ez);
             const float rij = v ? pu.rho : 0.f;
             const float2 rij2 = f2_splat(rij);
             float2 s2 = make_float2(0.f, 0.f);
@@ -146,20 +149,19 @@ __device__ __forceinline__ float tile_triples(const TabPair (*tab)[kTile / 2], c
                 const float2 wy = make_float2(t0.z, t0.w);
                 const float2 wz = make_float2(t1.x, t1.y);
                 const float2 rjk = make_float2(t1.z, t1.w);
-                float2 p1 = f2_mul(ux, vx[p]);
-                p1 = f2_fma(uy, vy[p], p1);
-                p1 = f2_fma(uz, vz[p], p1);
-                float2 p2 = f2_mul(ux, wx);
+                float2 p1 = f2_mul(u3x, vx[p]);                // -3 cos t_i
+                p1 = f2_fma(u3y, vy[p], p1);
+                p1 = f2_fma(u3z, vz[p], p1);
+                float2 p2 = f2_mul(ux, wx);                    // -cos t_j
                 p2 = f2_fma(uy, wy, p2);
                 p2 = f2_fma(uz, wz, p2);
-                float2 p3 = f2_mul(vx[p], wx);
+                float2 p3 = f2_mul(vx[p], wx);                 // cos t_k
                 p3 = f2_fma(vy[p], wy, p3);
                 p3 = f2_fma(vz[p], wz, p3);
-                const float2 t = f2_mul(f2_mul(p1, p2), p3);
-                const float2 n = f2_fma(t, m3, one);           // 1 + 3 cos cos cos
-                const float2 r2 = f2_mul(rk[p], rjk);          // rho_ik rho_jk
-                s2 = f2_fma(n, r2, s2);                        // row sum (x rho_ij later)
-                acc[p] = f2_fma(n, f2_mul(r2, rij2), acc[p]);  // column sums
+                const float2 t = f2_mul(f2_mul(p1, p2), p3);   // 3 cos cos cos
+                const float2 q = f2_fma(t, rjk, rjk);          // (1 + 3 cos cos cos) rho_jk
+                s2 = f2_fma(q, rk[p], s2);                     // row sum (x rho_ij later)
+                acc[p] = f2_fma(q, rij2, acc[p]);              // column sums (x rho_ik later)
             }
             const float srow = (s2.x + s2.y) * rij;
             acc_i += srow;
@@ -168,8 +170,9 @@ __device__ __forceinline__ float tile_triples(const TabPair (*tab)[kTile / 2], c
         }
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
-            redK[kb + 2 * p][lane] = acc[p].x;
-            redK[kb + 2 * p + 1][lane] = acc[p].y;
+            const float2 c = f2_mul(acc[p], rk[p]);
+            redK[kb + 2 * p][lane] = c.x;
+            redK[kb + 2 * p + 1][lane] = c.y;
         }
     }
     __syncwarp();
