@@ -7,3 +7,6 @@
 mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double eps, double alpha,
                               bool absolute, const mbm_config& cfg, mbm_tree* tree, double* phi,
                               mbm_stats* stats, cudaStream_t s);
+
+// Device bytes of one tree solve of N points (tree plus traversal scratch).
+size_t mbm_tree_solve_bytes(int64_t N, const mbm_config& cfg);

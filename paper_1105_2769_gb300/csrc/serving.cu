@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "mbm_internal.h"
+#include "mbm_tree_api.h"
 
 namespace {
 
@@ -67,14 +68,7 @@ size_t estimate_bytes(const mbm_request& r, const mbm_config& c) {
     const size_t io = N * 24 + N * (r.kind == MBM_REQ_FORCES ? 24 : 8);
     const int base = r.mode & 0xff;
     if (base != MBM_TREE) return io + N * 32 + 4096;
-    int depth = 0;
-    while ((((int64_t)N + ((int64_t)1 << depth) - 1) >> depth) > c.leaf_size) ++depth;
-    const size_t nodes = ((size_t)2 << depth);
-    const size_t tree = N * (8 + 24 + 32 + 8) + nodes * (24 * 3 + 16 + 128);
-    const size_t B = std::max<size_t>(1 << 14, std::min<size_t>(1 << 20, 2 * N));
-    const size_t trav = (size_t)(3 * depth + 8) * 4 * B * 16 + B * 64 + std::max<size_t>(4 * B, 1 << 22) * 16 +
-                        (3 * N + 65536) * 8 + N * 16 + nodes * 16;
-    return io + tree + trav + (1 << 20);
+    return io + mbm_tree_solve_bytes(r.N, c) + (1 << 20);
 }
 
 }  // namespace

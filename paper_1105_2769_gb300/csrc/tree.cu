@@ -294,30 +294,185 @@ seed_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_
                  flags);
 }
 
-// Base cases: leaf triples from the traversal's base list.
-__global__ void __launch_bounds__(kRangeWarps * 32)
-base_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_t N,
-            const int4* __restrict__ items, int64_t n_items, double* acc, int* flags,
-            unsigned long long* n_triples) {
+// Grouped base cases. One flush of the base list is sorted by its (y, z)
+// leaf pair (items are canonical, x <= y <= z), and every run of equal pair
+// is cut into pieces of at most kPiece items. A CTA takes a piece, builds the
+// (j,k) table of the pair once and its warps sweep the x leaves of the piece,
+// so the table and the (y, z) row sums are shared by up to kPiece leaf
+// triples. The arithmetic of every leaf triple is that of base_kernel.
+constexpr int kBaseWarps = 8;
+constexpr int kPiece = 64;
+
+// First particle of node v (recomputed where keeping it live costs registers).
+__device__ __noinline__ int64_t leaf_first(int64_t v, int64_t N) {
+    int64_t b, e;
+    node_range(v, N, b, e);
+    return b;
+}
+
+__device__ __forceinline__ unsigned leaf_triple_count(int x, int y, int z, unsigned n1,
+                                                      unsigned n2, unsigned n3) {
+    if (x == y && y == z) return n1 * (n1 - 1) * (n1 - 2) / 6;
+    if (x == y) return n1 * (n1 - 1) / 2 * n3;
+    if (y == z) return n1 * (n2 * (n2 - 1) / 2);
+    return n1 * n2 * n3;
+}
+
+// Sort keys of one flush, and the number of point triples it holds (Fig. 4
+// cases; at most 32^3 per leaf triple, summed per warp in 32 bits).
+__global__ void base_key_kernel(const int4* __restrict__ items, int64_t n, int64_t N,
+                                int64_t first_leaf, int d, ull* __restrict__ key,
+                                int* __restrict__ val, ull* __restrict__ n_triples) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t q0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t base = q0 - (threadIdx.x & 31); base < n; base += stride) {
+        const int64_t q = base + (threadIdx.x & 31);
+        unsigned c = 0;
+        if (q < n) {
+            const int4 t = items[q];
+            key[q] = ((ull)(t.y - first_leaf) << d) | (ull)(t.z - first_leaf);
+            val[q] = t.x;
+            int64_t b1, e1, b2, e2, b3, e3;
+            node_range(t.x, N, b1, e1);
+            node_range(t.y, N, b2, e2);
+            node_range(t.z, N, b3, e3);
+            c = leaf_triple_count(t.x, t.y, t.z, (unsigned)(e1 - b1), (unsigned)(e2 - b2),
+                                  (unsigned)(e3 - b3));
+        }
+        const unsigned w = __reduce_add_sync(0xffffffffu, c);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(n_triples, (ull)w);
+    }
+}
+
+// flag[q] = 1 where a piece starts: the first item of a run, and every
+// kPiece-th item after it (keys are sorted; the run start is found by
+// binary search).
+__global__ void base_piece_flag_kernel(const ull* __restrict__ key, int64_t n,
+                                       int* __restrict__ flag) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const ull k = key[q];
+        int64_t lo = 0, hi = q;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (key[mid] < k) lo = mid + 1;
+            else hi = mid;
+        }
+        flag[q] = ((q - lo) % kPiece) == 0 ? 1 : 0;
+    }
+}
+
+// heads[pos[q]] = q for every piece start; heads[n_pieces] = n.
+__global__ void base_piece_heads_kernel(const int* __restrict__ flag, const int* __restrict__ pos,
+                                        int64_t n, int* __restrict__ heads,
+                                        int* __restrict__ n_pieces) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (flag[q]) heads[pos[q]] = (int)q;
+        if (q == n - 1) {
+            const int np = pos[q] + flag[q];
+            heads[np] = (int)n;
+            *n_pieces = np;
+        }
+    }
+}
+
+struct BaseSmem {
+    mbm_tile::TabPair tab[kTile][kTile / 2];
+    float4 sJh[kTile], sJl[kTile], sKh[kTile], sKl[kTile];
+    float redJ[kBaseWarps][kTile][kTile + 1];
+    float redK[kBaseWarps][kTile][kTile + 1];
+    double wsum[2][kBaseWarps][kTile];
+    long long b2, b3;  // first particle of the y and z leaves
+    int Y, Z, n2, n3, st, en;
+};
+
+__global__ void __launch_bounds__(kBaseWarps * 32, 2)
+base_group_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_t N,
+                  int64_t first_leaf, int d, const ull* __restrict__ key,
+                  const int* __restrict__ val, const int* __restrict__ heads,
+                  const int* __restrict__ n_pieces_p, unsigned* __restrict__ piece_ctr,
+                  double* __restrict__ acc, int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem& w = reinterpret_cast<WarpSmem*>(smem_raw)[threadIdx.x >> 5];
-    const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (item >= n_items) return;
-    const int4 t = items[item];
-    int64_t b1, e1, b2, e2, b3, e3;
-    node_range(t.x, N, b1, e1);
-    node_range(t.y, N, b2, e2);
-    node_range(t.z, N, b3, e3);
-    range_triple(w, xh, xl, b1, (int)(e1 - b1), b2, (int)(e2 - b2), b3, (int)(e3 - b3), t.x == t.y,
-                 t.y == t.z, t.x == t.z, acc, flags);
-    if ((threadIdx.x & 31) == 0) {  // point triples of this leaf triple (Fig. 4 cases)
-        const unsigned long long n1 = e1 - b1, n2 = e2 - b2, n3 = e3 - b3;
-        unsigned long long c;
-        if (t.x == t.y && t.y == t.z) c = n1 * (n1 - 1) * (n1 - 2) / 6;
-        else if (t.x == t.y) c = n1 * (n1 - 1) / 2 * n3;
-        else if (t.y == t.z) c = n1 * (n2 * (n2 - 1) / 2);
-        else c = n1 * n2 * n3;
-        atomicAdd(n_triples, c);
+    BaseSmem& sm = *reinterpret_cast<BaseSmem*>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int n_pieces = *n_pieces_p;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int pc = (int)atomicAdd(piece_ctr, 1u);
+            sm.st = pc < n_pieces ? heads[pc] : -1;
+            if (pc < n_pieces) {
+                sm.en = heads[pc + 1];
+                const ull k = key[sm.st];
+                const int64_t Y = first_leaf + (int64_t)(k >> d);
+                const int64_t Z = first_leaf + (int64_t)(k & ((1ull << d) - 1));
+                int64_t b2, e2, b3, e3;
+                node_range(Y, N, b2, e2);
+                node_range(Z, N, b3, e3);
+                sm.Y = (int)Y;
+                sm.Z = (int)Z;
+                sm.b2 = b2;
+                sm.b3 = b3;
+                sm.n2 = (int)(e2 - b2);
+                sm.n3 = (int)(e3 - b3);
+            }
+        }
+        __syncthreads();
+        if (sm.st < 0) break;
+        if (threadIdx.x < kTile) {
+            const int n2 = sm.n2;
+            sm.sJh[threadIdx.x] = threadIdx.x < n2 ? xh[sm.b2 + threadIdx.x] : z4;
+            sm.sJl[threadIdx.x] = threadIdx.x < n2 ? xl[sm.b2 + threadIdx.x] : z4;
+        } else if (threadIdx.x < 2 * kTile) {
+            const int kk = threadIdx.x - kTile, n3 = sm.n3;
+            sm.sKh[kk] = kk < n3 ? xh[sm.b3 + kk] : z4;
+            sm.sKl[kk] = kk < n3 ? xl[sm.b3 + kk] : z4;
+        }
+        __syncthreads();
+        bool bad = false;
+        {
+            const int n2 = sm.n2, n3 = sm.n3;
+            const bool e23 = sm.Y == sm.Z;
+            for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+                const int jj = e >> 5, kk = e & 31;
+                const bool v = jj < n2 && kk < n3 && (!e23 || jj < kk);
+                bad |= mbm_tile::build_table_entry(sm.tab, jj, kk, sm.sJh[jj], sm.sJl[jj],
+                                                   sm.sKh[kk], sm.sKl[kk], v);
+            }
+        }
+        if (bad) atomicOr(flags, MBM_FLAG_COINCIDENT);
+        __syncthreads();
+        sm.wsum[0][warp][lane] = 0.0;
+        sm.wsum[1][warp][lane] = 0.0;
+        const int en = sm.en;
+        for (int q = sm.st + warp; q < en; q += kBaseWarps) {
+            const int X = val[q];
+            int64_t b1, e1;
+            node_range(X, N, b1, e1);
+            const int n1 = (int)(e1 - b1);
+            const bool iv = lane < n1;
+            const float4 ih = iv ? xh[b1 + lane] : z4;
+            const float4 il = iv ? xl[b1 + lane] : z4;
+            const float acc_i = mbm_tile::tile_triples(sm.tab, sm.sJh, sm.sJl, sm.sKh, sm.sKl, ih,
+                                                       il, iv, lane, sm.n2, sm.n3, X == sm.Y,
+                                                       X == sm.Z, sm.redJ[warp], sm.redK[warp]);
+            sm.wsum[0][warp][lane] += (double)mbm_tile::row_sum(sm.redJ[warp], lane);
+            sm.wsum[1][warp][lane] += (double)mbm_tile::row_sum(sm.redK[warp], lane);
+            __syncwarp();
+            if (iv) atomicAdd(&acc[leaf_first(X, N) + lane], (double)acc_i);
+        }
+        __syncthreads();
+        if (warp < 2) {
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < kBaseWarps; ++w) tot += sm.wsum[warp][w][lane];
+            const int nn = warp == 0 ? sm.n2 : sm.n3;
+            const long long b = warp == 0 ? sm.b2 : sm.b3;
+            if (lane < nn) atomicAdd(&acc[b + lane], tot);
+        }
+        __syncthreads();
     }
 }
 
@@ -1097,6 +1252,64 @@ size_t carve_size(const std::vector<size_t>& parts) {
     return mbm_align_up(s, 256);
 }
 
+std::vector<size_t> tree_parts(int64_t N, int64_t n_nodes) {
+    return {(size_t)N * 8, (size_t)N * 24, (size_t)N * 16, (size_t)N * 16,   // perm xs xh xl
+            (size_t)n_nodes * 24, (size_t)n_nodes * 24, (size_t)n_nodes * 24,  // lo hi cen
+            (size_t)n_nodes * 8, (size_t)n_nodes * 8, (size_t)N * 8,           // diam2 phil pphil
+            (size_t)n_nodes * 32 * 4};                                          // weak
+}
+
+// Buffer capacities of one traversal and its scratch layout.
+struct TravPlan {
+    int64_t B = 0, cap_lvl = 0, cap_mc = 0, cap_base = 0, cap_est = 0;
+    int max_levels = 0;
+    size_t cub_bytes = 0, sort_bytes = 0;
+    std::vector<size_t> parts;
+};
+
+TravPlan trav_plan(int64_t N, int depth, int m_limit, bool counting) {
+    TravPlan q;
+    const int64_t n_nodes = ((int64_t)2 << depth) - 1, n_leaves = (int64_t)1 << depth;
+    // Frontier chunk B: a chunk of B node triples yields at most 4B children,
+    // B Monte Carlo candidates and B base cases, so no list can overflow.
+    q.B = std::max<int64_t>(1 << 14, std::min<int64_t>(1 << 20, 2 * N));
+    q.max_levels = 3 * depth + 8;
+    q.cap_lvl = 4 * q.B;
+    q.cap_mc = q.B;
+    // Base list: large flushes give long runs of equal (y, z) leaf pairs to the
+    // grouped base kernel; never more than the number of canonical leaf
+    // triples, which bounds the whole traversal's base cases.
+    const double L = (double)n_leaves;
+    const double all = L * (L + 1.0) * (L + 2.0) / 6.0;
+    int64_t want = std::min<int64_t>(1 << 26, std::max<int64_t>(1 << 22, 512 * N));
+    if ((double)want > all) want = (int64_t)all;
+    q.cap_base = std::max<int64_t>(q.B, want);
+    q.cap_est = 3 * N + 64 * 1024;
+    cub::DeviceScan::ExclusiveSum(nullptr, q.cub_bytes, (int64_t*)nullptr, (int64_t*)nullptr,
+                                  (int)(q.cap_mc + 1));
+    // Base-case grouping: radix sort of (y, z) keys over 2 * depth bits and a
+    // scan of piece flags share one temporary buffer.
+    size_t scan_bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, q.sort_bytes, (ull*)nullptr, (ull*)nullptr,
+                                    (int*)nullptr, (int*)nullptr, (int)q.cap_base, 0,
+                                    std::max(1, 2 * depth));
+    cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, (int*)nullptr, (int*)nullptr,
+                                  (int)q.cap_base);
+    q.sort_bytes = std::max(q.sort_bytes, scan_bytes);
+    const size_t cb = (size_t)q.cap_base;
+    q.parts = {
+        (size_t)N * 8, (size_t)n_nodes * 8,                                // pt_acc node_acc
+        counting ? (size_t)N * 8 : 0, counting ? (size_t)n_nodes * 8 : 0,  // counts
+        (size_t)q.max_levels * q.cap_lvl * 16,                             // level buffers
+        (size_t)q.cap_mc * 16, cb * 16,                                    // mc, base
+        (size_t)(q.cap_mc + 2) * 8, (size_t)q.cap_mc * 4,                  // chunk_off, fail
+        (size_t)q.cap_est * 8, 256, q.cub_bytes,                           // est, counters
+        (size_t)(m_limit + 1) * 8,                                         // 1/m table
+        cb * 8, cb * 8, cb * 4, cb * 4,                                    // base keys, x
+        (cb + 1) * 4, (cb + 1) * 4, (cb + 1) * 4, 64, q.sort_bytes};       // flag pos heads
+    return q;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1120,11 +1333,7 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
     t->n_nodes = n_nodes;
     t->n_leaves = n_leaves;
     t->seed_levels = cfg.seed_levels;
-    const std::vector<size_t> parts = {
-        (size_t)N * 8, (size_t)N * 24, (size_t)N * 16, (size_t)N * 16,  // perm xs xh xl
-        (size_t)n_nodes * 24, (size_t)n_nodes * 24, (size_t)n_nodes * 24,  // lo hi cen
-        (size_t)n_nodes * 8, (size_t)n_nodes * 8, (size_t)N * 8,           // diam2 phil pphil
-        (size_t)n_nodes * 32 * 4};                                          // weak
+    const std::vector<size_t> parts = tree_parts(N, n_nodes);
     t->bytes = carve_size(parts);
     mbm_status st = mbm_budget_charge(ctx, t->bytes);
     if (st != MBM_OK) {
@@ -1347,26 +1556,15 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
 
     const int64_t n_nodes = tree->n_nodes, n_leaves = tree->n_leaves;
     const bool counting = cfg.tuple_counts != nullptr;
-    // Frontier chunk B: a chunk of B node triples yields at most 4B children,
-    // B Monte Carlo candidates and B base cases, so no list can overflow.
-    const int64_t B = std::max<int64_t>(1 << 14, std::min<int64_t>(1 << 20, 2 * N));
-    const int max_levels = 3 * tree->depth + 8;
-    const int64_t cap_lvl = 4 * B, cap_mc = B;
-    const int64_t cap_base = std::max<int64_t>(4 * B, 1 << 22);
-    const int64_t cap_est = 3 * N + 64 * 1024;
+    const TravPlan plan = trav_plan(N, tree->depth, cfg.m_limit, counting);
+    const int64_t B = plan.B, cap_lvl = plan.cap_lvl, cap_mc = plan.cap_mc;
+    const int64_t cap_base = plan.cap_base, cap_est = plan.cap_est;
+    const int max_levels = plan.max_levels;
+    size_t cub_bytes = plan.cub_bytes, sort_bytes = plan.sort_bytes;
+    const int d = tree->depth;
+    const int64_t first_leaf = n_nodes - n_leaves;
     const double z = z_two_sided(alpha);
-
-    size_t cub_bytes = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, cub_bytes, (int64_t*)nullptr, (int64_t*)nullptr,
-                                  (int)(cap_mc + 1), s);
-    const std::vector<size_t> parts = {
-        (size_t)N * 8, (size_t)n_nodes * 8,                                // pt_acc node_acc
-        counting ? (size_t)N * 8 : 0, counting ? (size_t)n_nodes * 8 : 0,  // counts
-        (size_t)max_levels * cap_lvl * 16,                                 // level buffers
-        (size_t)cap_mc * 16, (size_t)cap_base * 16,                        // mc, base
-        (size_t)(cap_mc + 2) * 8, (size_t)cap_mc * 4,                      // chunk_off, fail
-        (size_t)cap_est * 8, 256, cub_bytes,                               // est, counters
-        (size_t)(cfg.m_limit + 1) * 8};                                    // 1/m table
+    const std::vector<size_t>& parts = plan.parts;
     MBM_TRY(mbm_scratch_reserve(ctx, carve_size(parts)));
     Carve sc{static_cast<char*>(ctx->scratch)};
     double* pt_acc = sc.take<double>(N);
@@ -1382,6 +1580,15 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
     ull* ctr = sc.take<ull>(32);  // 0 n_next, 1 n_mc, 2 n_base, 3.. statistics
     void* cub_tmp = sc.take<char>(cub_bytes);
     double* rcp = sc.take<double>(cfg.m_limit + 1);
+    ull* bkey = sc.take<ull>(cap_base);
+    ull* bkey2 = sc.take<ull>(cap_base);
+    int* bval = sc.take<int>(cap_base);
+    int* bval2 = sc.take<int>(cap_base);
+    int* bflag = sc.take<int>(cap_base + 1);
+    int* bpos = sc.take<int>(cap_base + 1);
+    int* bheads = sc.take<int>(cap_base + 1);
+    int* bmeta = sc.take<int>(16);  // 0 n_pieces, 1 piece counter
+    void* sort_tmp = sc.take<char>(sort_bytes);
     ull* h = reinterpret_cast<ull*>(ctx->h_flags) + 8;  // pinned, after the status word
     {
         std::vector<double> r(cfg.m_limit + 1, 0.0);
@@ -1443,9 +1650,15 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
     p.base = basel;
     p.flags = ctx->d_flags;
 
-    const size_t wsm = sizeof(WarpSmem) * kRangeWarps;
-    MBM_CUDA_TRY(cudaFuncSetAttribute((const void*)base_kernel,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+    const size_t bsm = sizeof(BaseSmem);
+    MBM_CUDA_TRY(cudaFuncSetAttribute((const void*)base_group_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+    int base_per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&base_per_sm, base_group_kernel,
+                                                      kBaseWarps * 32, bsm) != cudaSuccess ||
+        base_per_sm < 1)
+        base_per_sm = 1;
+    const unsigned base_grid = (unsigned)(base_per_sm * std::max(1, ctx->num_sms));
     // Base cases run whenever the list could not take another chunk (Phi^l is
     // fixed, so base cases may run in any order); their time is accumulated.
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> base_ev;
@@ -1458,8 +1671,17 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
             cudaEventCreate(&b);
             cudaEventRecord(a, s);
         }
-        base_kernel<<<grid_of(n * 32, kRangeWarps * 32), kRangeWarps * 32, wsm, s>>>(
-            tree->xh, tree->xl, N, basel, n, pt_acc, ctx->d_flags, ctr + 12);
+        base_key_kernel<<<grid_of(n, 256), 256, 0, s>>>(basel, n, N, first_leaf, d, bkey, bval,
+                                                        ctr + 12);
+        MBM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(sort_tmp, sort_bytes, bkey, bkey2, bval,
+                                                     bval2, (int)n, 0, std::max(1, 2 * d), s));
+        base_piece_flag_kernel<<<grid_of(n, 256), 256, 0, s>>>(bkey2, n, bflag);
+        MBM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(sort_tmp, sort_bytes, bflag, bpos, (int)n, s));
+        base_piece_heads_kernel<<<grid_of(n, 256), 256, 0, s>>>(bflag, bpos, n, bheads, bmeta);
+        MBM_CUDA_TRY(cudaMemsetAsync(bmeta + 1, 0, sizeof(int), s));
+        base_group_kernel<<<base_grid, kBaseWarps * 32, bsm, s>>>(
+            tree->xh, tree->xl, N, first_leaf, d, bkey2, bval2, bheads, bmeta,
+            reinterpret_cast<unsigned*>(bmeta + 1), pt_acc, ctx->d_flags);
         MBM_CUDA_TRY(cudaGetLastError());
         if (tm.on) {
             cudaEventRecord(b, s);
@@ -1571,4 +1793,12 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
     }
     if (cfg.validate) return mbm_check_flags(ctx, s);
     return MBM_OK;
+}
+
+size_t mbm_tree_solve_bytes(int64_t N, const mbm_config& cfg) {
+    if (N < 3 || cfg.leaf_size < 2) return 0;
+    const int depth = tree_depth(N, cfg.leaf_size);
+    const int64_t n_nodes = ((int64_t)2 << depth) - 1;
+    const TravPlan plan = trav_plan(N, depth, cfg.m_limit, cfg.tuple_counts != nullptr);
+    return carve_size(tree_parts(N, n_nodes)) + carve_size(plan.parts);
 }
