@@ -193,17 +193,21 @@ def bench_fp64(api, inputs, torch, dev):
     return {"n": n64, "triples_per_s": triples(n64) / dt, "s": dt}
 
 
-def bench_tree(api, inputs, torch, dev, r64, np):
-    X = inputs.workload("gmm4_n65536")
+def bench_tree(api, inputs, torch, dev, r64, np, workload="gmm4_n65536", eps_list=(1e-2, 1e-1),
+               warm=True, n_sample=32):
+    """Tree solves (relative eps, alpha 0.05) timed end to end from device-resident X;
+    accuracy on n_sample seeded particles against the exact sampled sum."""
+    X = inputs.workload(workload)
     n = len(X)
     Xd = torch.from_numpy(X).to(dev)
-    idx = inputs.sample_indices(n, 32, 11)
+    idx = inputs.sample_indices(n, n_sample, 11)
     exact = api.potential_sampled(Xd, idx).cpu().numpy()
-    out = {"workload": "gmm4_n65536", "n": n, "alpha": 0.05, "sampled_particles": len(idx)}
+    out = {"workload": workload, "n": n, "alpha": 0.05, "sampled_particles": len(idx)}
     fp64_pps = n * r64 / triples(n)                       # plain FP64 exhaustive particles/s
     fp64_pps_config3 = N_CONFIG3 * r64 / triples(N_CONFIG3)
-    for eps in (1e-2, 1e-1):
-        api.potential(Xd, eps=eps, alpha=0.05, mode="tree")  # warm-up
+    for eps in eps_list:
+        if warm:
+            api.potential(Xd, eps=eps, alpha=0.05, mode="tree")  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         phi, st = api.potential(Xd, eps=eps, alpha=0.05, mode="tree", stats=True)
@@ -285,6 +289,21 @@ def bench_serving(api, inputs, np, duration=6.0, rate=200.0):
             "mix": "70% tree Phi (eps 1e-2, alpha 0.05, resident systems), 30% FP32 forces"}
 
 
+def run_tree_only(args):
+    import numpy as np
+    import torch
+
+    from paper_1105_2769_gb300 import api, inputs
+    dev = torch.device("cuda", 0)
+    fp64 = bench_fp64(api, inputs, torch, dev)
+    eps_list = tuple(float(e) for e in args.tree_eps.split(","))
+    rep = bench_tree(api, inputs, torch, dev, fp64["triples_per_s"], np, workload=args.tree_only,
+                     eps_list=eps_list, warm=False, n_sample=args.tree_sample)
+    rep["fp64_exhaustive"] = fp64
+    print(json.dumps({"report": "tree", **rep}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -293,9 +312,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip FP64/tree/forces/serving")
+    ap.add_argument("--tree-only", metavar="WORKLOAD", default=None,
+                    help="only time tree solves of this workload (e.g. gmm_n1048576), one "
+                         "solve per eps without warm-up, and print their JSON report")
+    ap.add_argument("--tree-eps", default="1e-2,1e-1")
+    ap.add_argument("--tree-sample", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.tree_only:
+        return run_tree_only(args)
 
     import numpy as np
     import torch

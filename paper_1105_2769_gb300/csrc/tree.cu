@@ -7,23 +7,31 @@
 //   seed            : Phi^l (Sec. 4 summary statistic, read as a lower bound on
 //                     |Phi|): |exact sum over each particle's seed node|, min
 //                     over every node (Sec. 5: Phi^l(P) = min over children).
-//   a5/a6 traversal : breadth-first over node triples from (root, root, root);
-//                     per triple the p = 0 interval bound, T_i of Fig. 4 and
-//                     the budget of Eq. (deterministic_prune) decide: prune
-//                     (accumulate T_i phi(c1,c2,c3) per node), Monte Carlo
-//                     candidate, base case, or split the largest-diameter
-//                     node (all of its copies; non-decreasing child triples).
+//   a5/a6 traversal : node triples from (root, root, root), one thread each,
+//                     in chunks of B triples taken from a stack of level
+//                     buffers (the deepest level first, so memory stays
+//                     bounded); per triple the p = 0 interval bound, T_i of
+//                     Fig. 4 and the budget of Eq. (deterministic_prune)
+//                     decide: prune (accumulate T_i phi(c1,c2,c3) per node),
+//                     Monte Carlo candidate, base case, or split the
+//                     largest-diameter node (all of its copies;
+//                     non-decreasing child triples).
 //   a7 Monte Carlo  : Algorithms 3-5; a lane per particle draws tuples with
 //                     Philox-4x32-10, FP32 phi, FP64 Welford statistics and
-//                     stop test; a triple passes only if all its particles do.
+//                     stop test; a triple passes only if all its particles do,
+//                     so each candidate first tests its 8 weakest particles
+//                     (smallest Phi^l) per node and stops at the first failure.
 //   a8 base cases   : exhaustive leaf triples with the Fig. 4 masks, FP32 bulk
-//                     (tile_fp32.cuh), FP64 accumulation.
+//                     (tile_fp32.cuh), FP64 accumulation; each flush of the
+//                     base list is sorted by (y, z) leaf pair so a CTA shares
+//                     one (j,k) table across the x leaves of a pair.
 //   a9 top-down     : node accumulators summed along each leaf's root path.
 //
-// Every decision is computed in FP64 in the same operation order as the
+// Every bound decision is computed in FP64 in the same operation order as the
 // serial restatement (explicit round-to-nearest intrinsics, no contraction),
-// and Phi^l is fixed before the traversal, so the breadth-first order makes
-// the same decisions as a depth-first recursion.
+// and Phi^l is fixed before the traversal, so this order makes the same
+// decisions as a depth-first recursion. Monte Carlo samples are FP32 phi
+// values, so a stop test on the edge may rarely differ from an FP64 sample.
 #include <cub/cub.cuh>
 
 #include <algorithm>
@@ -988,6 +996,15 @@ __device__ double mc_warp(const Trav& p, const int64_t P[3], const int64_t bb[3]
                   p.tau),
         p.inv_troot);
     const double reject_v = __dmul_rn(__dmul_rn(rhs_max, rhs_max) / (p.z * p.z), 1.0 + 1e-9);
+    // m2 never decreases with m, so at every later m' <= m_limit the variance
+    // of the mean is at least m2 / ((m_limit - 1) m_limit). Once that exceeds
+    // reject_v the stop test cannot pass any more and the particle would fail
+    // at m_limit: it fails now (same decision, fewer samples). An update of
+    // m2 can round below zero only when a sample lies within a few ulps of
+    // the mean, by at most ~ulp(mean)^2 per sample; the relative and the
+    // mean^2 slack cover m_limit such updates.
+    const double hopeless_m2 =
+        __dmul_rn(__dmul_rn(reject_v, (double)(p.m_limit - 1) * (double)p.m_limit), 1.0 + 1e-9);
     double mean = 0.0, m2 = 0.0;
     int m = 0;
     bool pass = false, done = !active;
@@ -1013,7 +1030,10 @@ __device__ double mc_warp(const Trav& p, const int64_t P[3], const int64_t bb[3]
             m2 = __dadd_rn(m2, __dmul_rn(dlt, __dsub_rn(f, mean)));
             const bool testing = m >= 2 && (m >= 30 || m >= p.m_limit);
             const double var_mu = testing ? __dmul_rn(__dmul_rn(m2, p.rcp[m - 1]), p.rcp[m]) : 0.0;
-            if (testing && var_mu > reject_v) {  // cannot pass at this m
+            if (m >= 2 && m2 > hopeless_m2 + 1e-20 * mean * mean) {  // no later m can pass
+                pass = false;
+                done = true;
+            } else if (testing && var_mu > reject_v) {  // cannot pass at this m
                 pass = false;
                 if (m >= p.m_limit) done = true;
             } else if (testing) {  // the test can end the loop only here

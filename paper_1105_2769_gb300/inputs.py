@@ -197,6 +197,8 @@ def workload(name: str, return_stats: bool = False):
                       components (16 384 points each, as there) in a cube of
                       side 100 (4/64)^(1/3), so component density and
                       per-component structure match the 2^20 set; seed 3
+    gmm16_n262144   : the same with 16 components (262 144 points) in a cube
+                      of side 100 (16/64)^(1/3); seed 3
     """
     if name == "exh64_n512":
         r = uniform_cube(512, 1.0, 0.01, 1, return_stats=True)
@@ -208,6 +210,9 @@ def workload(name: str, return_stats: bool = False):
         r = uniform_cube(65536, 32.0, 0.5, 4, return_stats=True)
     elif name == "gmm4_n65536":
         r = gaussian_mixture(65536, 4, 100.0 * (4 / 64) ** (1 / 3), 0.5, 3.0, 0.05, 3,
+                             return_stats=True)
+    elif name == "gmm16_n262144":
+        r = gaussian_mixture(1 << 18, 16, 100.0 * (16 / 64) ** (1 / 3), 0.5, 3.0, 0.05, 3,
                              return_stats=True)
     else:
         raise KeyError(name)
