@@ -194,7 +194,7 @@ def bench_fp64(api, inputs, torch, dev):
 
 
 def bench_tree(api, inputs, torch, dev, r64, np, workload="gmm4_n65536", eps_list=(1e-2, 1e-1),
-               warm=True, n_sample=32):
+               warm=True, n_sample=32, progress=False):
     """Tree solves (relative eps, alpha 0.05) timed end to end from device-resident X;
     accuracy on n_sample seeded particles against the exact sampled sum."""
     X = inputs.workload(workload)
@@ -221,6 +221,9 @@ def bench_tree(api, inputs, torch, dev, r64, np, workload="gmm4_n65536", eps_lis
                          ("ms_build", "ms_traverse", "ms_base", "ms_finalize")},
             "det_prunes": st["det_prunes"], "mc_prunes": st["mc_prunes"],
             "base_triples": st["base_triples"], "mc_samples": st["mc_samples"]}
+        if progress:
+            print(json.dumps({"progress": workload, f"eps_{eps:g}": out[f"eps_{eps:g}"]}),
+                  flush=True)
     out["fp64_exhaustive_particles_per_s"] = fp64_pps
     out["fp64_exhaustive_particles_per_s_n1048576"] = fp64_pps_config3
     return out
@@ -298,7 +301,7 @@ def run_tree_only(args):
     fp64 = bench_fp64(api, inputs, torch, dev)
     eps_list = tuple(float(e) for e in args.tree_eps.split(","))
     rep = bench_tree(api, inputs, torch, dev, fp64["triples_per_s"], np, workload=args.tree_only,
-                     eps_list=eps_list, warm=False, n_sample=args.tree_sample)
+                     eps_list=eps_list, warm=False, n_sample=args.tree_sample, progress=True)
     rep["fp64_exhaustive"] = fp64
     print(json.dumps({"report": "tree", **rep}))
     return 0

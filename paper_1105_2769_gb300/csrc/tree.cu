@@ -308,7 +308,7 @@ seed_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_
 // (j,k) table of the pair once and its warps sweep the x leaves of the piece,
 // so the table and the (y, z) row sums are shared by up to kPiece leaf
 // triples. The arithmetic of every leaf triple is that of base_kernel.
-constexpr int kBaseWarps = 8;
+constexpr int kBaseWarps = 4;
 constexpr int kPiece = 64;
 
 // First particle of node v (recomputed where keeping it live costs registers).
@@ -395,7 +395,7 @@ struct BaseSmem {
     int Y, Z, n2, n3, st, en;
 };
 
-__global__ void __launch_bounds__(kBaseWarps * 32, 2)
+__global__ void __launch_bounds__(kBaseWarps * 32, 4)
 base_group_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_t N,
                   int64_t first_leaf, int d, const ull* __restrict__ key,
                   const int* __restrict__ val, const int* __restrict__ heads,
@@ -1301,7 +1301,7 @@ TravPlan trav_plan(int64_t N, int depth, int m_limit, bool counting) {
     // triples, which bounds the whole traversal's base cases.
     const double L = (double)n_leaves;
     const double all = L * (L + 1.0) * (L + 2.0) / 6.0;
-    int64_t want = std::min<int64_t>(1 << 26, std::max<int64_t>(1 << 22, 512 * N));
+    int64_t want = std::min<int64_t>(1 << 27, std::max<int64_t>(1 << 22, 512 * N));
     if ((double)want > all) want = (int64_t)all;
     q.cap_base = std::max<int64_t>(q.B, want);
     q.cap_est = 3 * N + 64 * 1024;
