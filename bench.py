@@ -277,10 +277,11 @@ def bench_serving(api, inputs, np, duration=6.0, rate=200.0):
                                       system_id=int(picks[q]) + 1))
         else:
             tickets.append(srv.submit(X, kind="forces", mode="fp32"))
-    lat = []
-    for t in tickets:
+    lat, comp_tree, comp_forces = [], [], []
+    for q, t in enumerate(tickets):
         st, res, _ = srv.poll(t)
         lat.append(res["latency_ms"])
+        (comp_tree if kinds[q] else comp_forces).append(res["compute_ms"])
     wall = time.perf_counter() - t_start
     stats = srv.stats()
     srv.close()
@@ -289,6 +290,9 @@ def bench_serving(api, inputs, np, duration=6.0, rate=200.0):
             "p99_ms": float(np.percentile(lat, 99)), "wall_s": wall, "slots": 8,
             "n_range": [1024, 4096], "admitted": stats["admitted"],
             "rejected": stats["rejected"],
+            "compute_ms_p50": {"tree": float(np.percentile(comp_tree, 50)) if comp_tree else None,
+                               "forces": float(np.percentile(comp_forces, 50))
+                               if comp_forces else None},
             "mix": "70% tree Phi (eps 1e-2, alpha 0.05, resident systems), 30% FP32 forces"}
 
 

@@ -1006,7 +1006,7 @@ __device__ double mc_warp(const Trav& p, const int64_t P[3], const int64_t bb[3]
     const double hopeless_m2 =
         __dmul_rn(__dmul_rn(reject_v, (double)(p.m_limit - 1) * (double)p.m_limit), 1.0 + 1e-9);
     double mean = 0.0, m2 = 0.0;
-    int m = 0;
+    int m = 0, next_test = 30;
     bool pass = false, done = !active;
     int samples = 0, iter = 0;
     uint32_t rr[4] = {0, 0, 0, 0};
@@ -1025,17 +1025,34 @@ __device__ double mc_warp(const Trav& p, const int64_t P[3], const int64_t bb[3]
             const double f = (double)phi_fp32(p.xh, p.xl, x, y, zz);
             ++m;
             ++samples;
+            // Welford updates of the running mean and sum of squares (fused)
             const double dlt = __dsub_rn(f, mean);
-            mean = __dadd_rn(mean, __dmul_rn(dlt, p.rcp[m]));
-            m2 = __dadd_rn(m2, __dmul_rn(dlt, __dsub_rn(f, mean)));
-            const bool testing = m >= 2 && (m >= 30 || m >= p.m_limit);
+            mean = __fma_rn(dlt, p.rcp[m], mean);
+            m2 = __fma_rn(dlt, __dsub_rn(f, mean), m2);
+            // Tests before next_test are skipped: each would fail the
+            // variance comparison below (m2 never decreases).
+            const bool testing = m >= 2 && ((m >= 30 && m >= next_test) || m >= p.m_limit);
             const double var_mu = testing ? __dmul_rn(__dmul_rn(m2, p.rcp[m - 1]), p.rcp[m]) : 0.0;
-            if (m >= 2 && m2 > hopeless_m2 + 1e-20 * mean * mean) {  // no later m can pass
+            if (m >= 2 && m2 > hopeless_m2 &&
+                m2 > hopeless_m2 + 1e-20 * mean * mean) {  // no later m can pass
                 pass = false;
                 done = true;
             } else if (testing && var_mu > reject_v) {  // cannot pass at this m
                 pass = false;
-                if (m >= p.m_limit) done = true;
+                if (m >= p.m_limit) {
+                    done = true;
+                } else if (reject_v > 0.0) {
+                    // The first m' that can pass has (m'-1) m' >= m2 / reject_v; the
+                    // root is taken in FP32 from a bound shrunk by 1e-4 (and by the
+                    // rounding slack of m2), so every skipped m' would fail here.
+                    const float K =
+                        (float)((m2 - 1e-20 * mean * mean) / reject_v) * 0.9999f;
+                    if (K > 0.0f) {
+                        const float root = 0.5f * (1.0f + sqrtf(fmaf(4.0f, K, 1.0f)));
+                        const int nt = root < (float)p.m_limit ? (int)root : p.m_limit;
+                        if (nt > next_test) next_test = nt;
+                    }
+                }
             } else if (testing) {  // the test can end the loop only here
                 // sigma_mu = sqrt(m2 / (m-1) / m), with exact reciprocals
                 const double sig = __dsqrt_rn(var_mu);
