@@ -1356,7 +1356,7 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
                              cudaStream_t s, mbm_tree** out) {
     if (N < 3) return mbm_fail(MBM_EINVAL, "tree needs N >= 3");
     if (cfg.leaf_size < 2 || cfg.leaf_size > kTile) return mbm_fail(MBM_EINVAL, "leaf_size must be in [2, 32]");
-    if (cfg.seed_levels < 0 || cfg.seed_levels > 4) return mbm_fail(MBM_EINVAL, "seed_levels must be in [0, 4]");
+    if (cfg.seed_levels < 0 || cfg.seed_levels > 7) return mbm_fail(MBM_EINVAL, "seed_levels must be in [0, 7]");
     const int depth = tree_depth(N, cfg.leaf_size);
     const int64_t n_nodes = ((int64_t)2 << depth) - 1, n_leaves = (int64_t)1 << depth;
     if (n_nodes >= (1 << 24)) return mbm_fail(MBM_EINVAL, "tree too large (node ids are 24-bit)");
@@ -1402,9 +1402,12 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
     cub::DeviceRadixSort::SortPairs(nullptr, cub_bytes, (uint64_t*)nullptr, (uint64_t*)nullptr,
                                     (int*)nullptr, (int*)nullptr, (int)N, 0, 63, s);
     const int sd = std::max(0, depth - cfg.seed_levels);
+    const int64_t max_seed = (N + ((int64_t)1 << sd) - 1) >> sd;  // ceil(N / 2^sd)
+    const int chunks = (int)((max_seed + kTile - 1) / kTile);
+    const std::vector<int4> cmb = chunk_combos(chunks);
     const std::vector<size_t> sparts = {(size_t)nb * 48, 64, (size_t)N * 8, (size_t)N * 8,
                                         (size_t)N * 4, (size_t)N * 4, cub_bytes, (size_t)N * 8,
-                                        1024 * 16};
+                                        cmb.size() * 16};
     st = mbm_scratch_reserve(ctx, carve_size(sparts));
     if (st != MBM_OK) {
         mbm_tree_free(t);
@@ -1419,7 +1422,7 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
     int* i1 = sc.take<int>(N);
     void* cub_tmp = sc.take<char>(cub_bytes);
     double* seed = sc.take<double>(N);
-    int4* combos = sc.take<int4>(1024);
+    int4* combos = sc.take<int4>(cmb.size());
 
 #define TRY_LAUNCH()                                                           \
     do {                                                                       \
@@ -1453,13 +1456,6 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
     TRY_LAUNCH();
 
     // Phi^l seed: exact sums over triples inside each seed node.
-    const int64_t max_seed = (N + ((int64_t)1 << sd) - 1) >> sd;  // ceil(N / 2^sd)
-    const int chunks = (int)((max_seed + kTile - 1) / kTile);
-    std::vector<int4> cmb = chunk_combos(chunks);
-    if (cmb.size() > 1024) {
-        mbm_tree_free(t);
-        return mbm_fail(MBM_EINVAL, "seed node too large");
-    }
     e = cudaMemcpyAsync(combos, cmb.data(), cmb.size() * sizeof(int4), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(seed, 0, (size_t)N * 8, s);
     if (e != cudaSuccess) {

@@ -40,6 +40,8 @@ def gmm():
 
 
 def _gpu_tree(X, eps, alpha, mode="tree", **cfg):
+    # the oracle's default seed node (3 levels above the leaves) unless given
+    cfg.setdefault("seed_levels", 3)
     Xd = torch.from_numpy(X).cuda()
     counts = torch.zeros(len(X), dtype=torch.int64, device="cuda")
     phi, st = api.potential(Xd, eps=eps, alpha=alpha, mode=mode, config=api.tree_config(**cfg),
@@ -55,9 +57,10 @@ def test_tree_layout_matches_definition(gmm):
     assert np.array_equal(got["perm"], ref["perm"])
     assert np.array_equal(got["lo"], ref["lo"]) and np.array_equal(got["hi"], ref["hi"])
     np.testing.assert_allclose(got["cen"], ref["cen"], rtol=1e-13, atol=1e-12)
-    # Phi^l seed: |exact sum over the seed node (3 levels above the leaves)|, min per node
+    # Phi^l seed: |exact sum over the seed node (the default number of levels
+    # above the leaves)|, min per node
     d = ref["depth"]
-    sd = max(0, d - 3)
+    sd = max(0, d - _lib.default_config().seed_levels)
     seed = np.zeros(len(X))
     seed_abs = np.zeros(len(X))
     for q in range(1 << sd):
@@ -149,3 +152,5 @@ def test_bad_arguments(gmm):
         api.potential(Xd, eps=-1.0, mode="tree")
     with pytest.raises(_lib.MbmError):
         api.potential(Xd, eps=0.1, mode="tree", config=api.tree_config(leaf_size=64))
+    with pytest.raises(_lib.MbmError):
+        api.potential(Xd, eps=0.1, mode="tree", config=api.tree_config(seed_levels=8))
