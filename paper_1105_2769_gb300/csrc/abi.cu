@@ -186,7 +186,7 @@ static mbm_status run_exhaustive(mbm_ctx* ctx, const double* X, int64_t N, int m
                                  int validate, cudaStream_t s) {
     const size_t hdr = 256;  // work counter
     const size_t pack = mode == MBM_EXH_FP32 ? (size_t)N * 2 * sizeof(float4)
-                                             : (size_t)N * sizeof(double4);
+                                             : (size_t)N * sizeof(double4_32a);
     MBM_TRY(mbm_scratch_reserve(ctx, hdr + pack));
     char* base = static_cast<char*>(ctx->scratch);
     auto* counter = reinterpret_cast<unsigned long long*>(base);
@@ -201,7 +201,7 @@ static mbm_status run_exhaustive(mbm_ctx* ctx, const double* X, int64_t N, int m
         MBM_CUDA_TRY(launch_exh_fp32(xh, xl, N, phi, counter, ctx->d_flags, ctx->num_sms, s));
         mbm_time_end(ctx, s);
     } else {
-        auto* x4 = reinterpret_cast<double4*>(base + hdr);
+        auto* x4 = reinterpret_cast<double4_32a*>(base + hdr);
         MBM_CUDA_TRY(launch_pack_f64(X, N, x4, ctx->d_flags, s));
         mbm_time_begin(ctx, s);
         MBM_CUDA_TRY(launch_exh_fp64(x4, N, phi, counter, ctx->d_flags, ctx->num_sms, s));

@@ -69,7 +69,7 @@ struct PairU64 {
     double ex, ey, ez, rho, i3;
 };
 
-__device__ __forceinline__ PairU64 pair64(double4 p, double4 q, bool& ok) {
+__device__ __forceinline__ PairU64 pair64(double4_32a p, double4_32a q, bool& ok) {
     const double dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
     const double s = dx * dx + dy * dy + dz * dz;
     ok = s > 0.0;
@@ -89,7 +89,7 @@ struct Pts32 {
     const float4* xl;
 };
 struct Pts64 {
-    const double4* x;
+    const double4_32a* x;
 };
 
 template <typename Real, int KSUB, typename Pts>
@@ -115,7 +115,7 @@ adjoint_kernel(Pts pts, int N, int NT, const double* __restrict__ g, long long p
             }
         } else {
             if (iv) {
-                const double4 a = pts.x[i];
+                const double4_32a a = pts.x[i];
                 xi = {a.x, a.y, a.z, 0.0};
             }
         }
@@ -136,7 +136,7 @@ adjoint_kernel(Pts pts, int N, int NT, const double* __restrict__ g, long long p
                     sm.sJ[jj] = {a.x, a.y, a.z, 0.f};
                     sm.sJl[jj] = {b.x, b.y, b.z, 0.f};
                 } else {
-                    const double4 a = jj < nJ ? pts.x[j] : make_double4(0, 0, 0, 0);
+                    const double4_32a a = jj < nJ ? pts.x[j] : make_double4_32a(0, 0, 0, 0);
                     sm.sJ[jj] = {a.x, a.y, a.z, 0.0};
                 }
                 sm.gJ[jj] = (g && jj < nJ) ? (Real)g[j] : (Real)0;
@@ -148,7 +148,7 @@ adjoint_kernel(Pts pts, int N, int NT, const double* __restrict__ g, long long p
                     sm.sK[kk] = {a.x, a.y, a.z, 0.f};
                     sm.sKl[kk] = {b.x, b.y, b.z, 0.f};
                 } else {
-                    const double4 a = kk < nK ? pts.x[k] : make_double4(0, 0, 0, 0);
+                    const double4_32a a = kk < nK ? pts.x[k] : make_double4_32a(0, 0, 0, 0);
                     sm.sK[kk] = {a.x, a.y, a.z, 0.0};
                 }
                 sm.gK[kk] = (g && kk < nK) ? (Real)g[k] : (Real)0;
@@ -167,8 +167,8 @@ adjoint_kernel(Pts pts, int N, int NT, const double* __restrict__ g, long long p
                                               ok);
                     if (v && ok) ent = {pr.ex, pr.ey, pr.ez, pr.rho};
                 } else {
-                    const PairU64 pr = pair64(make_double4(sm.sJ[jj].x, sm.sJ[jj].y, sm.sJ[jj].z, 0),
-                                              make_double4(sm.sK[kk].x, sm.sK[kk].y, sm.sK[kk].z, 0),
+                    const PairU64 pr = pair64(make_double4_32a(sm.sJ[jj].x, sm.sJ[jj].y, sm.sJ[jj].z, 0),
+                                              make_double4_32a(sm.sK[kk].x, sm.sK[kk].y, sm.sK[kk].z, 0),
                                               ok);
                     if (v && ok) ent = {pr.ex, pr.ey, pr.ez, pr.rho};
                 }
@@ -194,8 +194,8 @@ adjoint_kernel(Pts pts, int N, int NT, const double* __restrict__ g, long long p
                                                   ok);
                         ex = pr.ex; ey = pr.ey; ez = pr.ez; rho = pr.rho; i3 = pr.i3;
                     } else {
-                        const PairU64 pr = pair64(make_double4(xi.x, xi.y, xi.z, 0),
-                                                  make_double4(sm.sK[kk].x, sm.sK[kk].y, sm.sK[kk].z, 0),
+                        const PairU64 pr = pair64(make_double4_32a(xi.x, xi.y, xi.z, 0),
+                                                  make_double4_32a(sm.sK[kk].x, sm.sK[kk].y, sm.sK[kk].z, 0),
                                                   ok);
                         ex = pr.ex; ey = pr.ey; ez = pr.ez; rho = pr.rho; i3 = pr.i3;
                     }
@@ -219,8 +219,8 @@ adjoint_kernel(Pts pts, int N, int NT, const double* __restrict__ g, long long p
                                                   ok);
                         ux = pr.ex; uy = pr.ey; uz = pr.ez; ru = pr.rho; su = pr.i3;
                     } else {
-                        const PairU64 pr = pair64(make_double4(xi.x, xi.y, xi.z, 0),
-                                                  make_double4(sm.sJ[jj].x, sm.sJ[jj].y, sm.sJ[jj].z, 0),
+                        const PairU64 pr = pair64(make_double4_32a(xi.x, xi.y, xi.z, 0),
+                                                  make_double4_32a(sm.sJ[jj].x, sm.sJ[jj].y, sm.sJ[jj].z, 0),
                                                   ok);
                         ux = pr.ex; uy = pr.ey; uz = pr.ez; ru = pr.rho; su = pr.i3;
                     }
@@ -273,12 +273,12 @@ adjoint_kernel(Pts pts, int N, int NT, const double* __restrict__ g, long long p
     }
 }
 
-__global__ void pack64_kernel(const double* __restrict__ X, int64_t N, double4* x4, int* flags) {
+__global__ void pack64_kernel(const double* __restrict__ X, int64_t N, double4_32a* x4, int* flags) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
         if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(flags, MBM_FLAG_NONFINITE);
-        x4[i] = make_double4(x, y, z, 0.0);
+        x4[i] = make_double4_32a(x, y, z, 0.0);
     }
 }
 
@@ -313,7 +313,7 @@ mbm_status run_adjoint(mbm_ctx* ctx, const double* X, int64_t N, const double* g
     MBM_CUDA_TRY(cudaMemsetAsync(out, 0, (size_t)N * 3 * sizeof(double), s));
     if (N < 3) return MBM_OK;
     const size_t pack = mode == MBM_EXH_FP32 ? (size_t)N * 2 * sizeof(float4)
-                                             : (size_t)N * sizeof(double4);
+                                             : (size_t)N * sizeof(double4_32a);
     MBM_TRY(mbm_scratch_reserve(ctx, 256 + pack));
     char* base = static_cast<char*>(ctx->scratch) + 256;
     MBM_CUDA_TRY(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
@@ -324,7 +324,7 @@ mbm_status run_adjoint(mbm_ctx* ctx, const double* X, int64_t N, const double* g
         MBM_CUDA_TRY(launch_pack_hilo(X, N, xh, xl, ctx->d_flags, s));
         MBM_CUDA_TRY((launch_adjoint<float, 16>(Pts32{xh, xl}, N, g, out, sign, ctx->num_sms, s)));
     } else {
-        auto* x4 = reinterpret_cast<double4*>(base);
+        auto* x4 = reinterpret_cast<double4_32a*>(base);
         const int64_t blocks = (N + 255) / 256;
         pack64_kernel<<<(unsigned)(blocks < 65535 ? blocks : 65535), 256, 0, s>>>(X, N, x4,
                                                                                  ctx->d_flags);

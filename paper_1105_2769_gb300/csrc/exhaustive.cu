@@ -47,13 +47,13 @@ __global__ void pack_hilo_kernel(const double* __restrict__ X, int64_t N, float4
     }
 }
 
-__global__ void pack_f64_kernel(const double* __restrict__ X, int64_t N, double4* __restrict__ x4,
+__global__ void pack_f64_kernel(const double* __restrict__ X, int64_t N, double4_32a* __restrict__ x4,
                                 int* __restrict__ flags) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
         if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(flags, MBM_FLAG_NONFINITE);
-        x4[i] = make_double4(x, y, z, 0.0);
+        x4[i] = make_double4_32a(x, y, z, 0.0);
     }
 }
 
@@ -148,19 +148,19 @@ struct Fp64Smem {
     double2 bw[kWarps64][kTile][kTile];    // (b, B) for (k, lane)
     double red[kWarps64][kTile][kTile + 1];
     double wsum[2][kWarps64][kTile];
-    double4 sJ[kTile], sK[kTile];
+    double4_32a sJ[kTile], sK[kTile];
     long long item;
 };
 
 __global__ void __launch_bounds__(kWarps64 * 32, 1)
-exh_fp64_kernel(const double4* __restrict__ x4, int N, int NT, long long n_items,
+exh_fp64_kernel(const double4_32a* __restrict__ x4, int N, int NT, long long n_items,
                 unsigned long long* __restrict__ counter, double* __restrict__ phi,
                 int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Fp64Smem& sm = *reinterpret_cast<Fp64Smem*>(smem_raw);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const double4 zero4 = make_double4(0.0, 0.0, 0.0, 0.0);
+    const double4_32a zero4 = make_double4_32a(0.0, 0.0, 0.0, 0.0);
 
     for (;;) {
         if (threadIdx.x == 0) sm.item = (long long)atomicAdd(counter, 1ULL);
@@ -201,7 +201,7 @@ exh_fp64_kernel(const double4* __restrict__ x4, int N, int NT, long long n_items
         for (int I = warp; I <= J; I += kWarps64) {
             const int i = I * kTile + lane;
             const bool iv = i < N;
-            const double4 xi = iv ? x4[i] : zero4;
+            const double4_32a xi = iv ? x4[i] : zero4;
 #pragma unroll 4
             for (int kk = 0; kk < kTile; ++kk) {
                 const bool v = iv && (K * kTile + kk < N) && (I != K || lane < kk);
@@ -347,7 +347,7 @@ cudaError_t launch_pack_hilo(const double* X, int64_t N, float4* xhi, float4* xl
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_f64(const double* X, int64_t N, double4* x4, int* flags, cudaStream_t s) {
+cudaError_t launch_pack_f64(const double* X, int64_t N, double4_32a* x4, int* flags, cudaStream_t s) {
     if (N <= 0) return cudaSuccess;
     const int threads = 256;
     const long long blocks = (N + threads - 1) / threads;
@@ -370,7 +370,7 @@ cudaError_t launch_exh_fp32(const float4* xhi, const float4* xlo, int64_t N, dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_exh_fp64(const double4* x4, int64_t N, double* phi, unsigned long long* counter,
+cudaError_t launch_exh_fp64(const double4_32a* x4, int64_t N, double* phi, unsigned long long* counter,
                             int* flags, int num_sms, cudaStream_t s) {
     const int NT = (int)((N + kTile - 1) / kTile);
     const long long items = (long long)NT * (NT + 1) / 2;

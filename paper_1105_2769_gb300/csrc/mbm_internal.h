@@ -78,14 +78,14 @@ static inline size_t mbm_align_up(size_t x, size_t a) { return (x + a - 1) / a *
 cudaError_t launch_pack_hilo(const double* X, int64_t N, float4* xhi, float4* xlo, int* flags,
                              cudaStream_t s);
 // Input pack to FP64 float4-like (x, y, z, 0) double quads.
-cudaError_t launch_pack_f64(const double* X, int64_t N, double4* x4, int* flags, cudaStream_t s);
+cudaError_t launch_pack_f64(const double* X, int64_t N, double4_32a* x4, int* flags, cudaStream_t s);
 
 // Exhaustive sums (steps a2/a3). phi must be zeroed by the caller.
 // counter: one zeroed unsigned long long of scratch for dynamic scheduling.
 cudaError_t launch_exh_fp32(const float4* xhi, const float4* xlo, int64_t N, double* phi,
                             unsigned long long* counter, int* flags, int num_sms,
                             cudaStream_t s);
-cudaError_t launch_exh_fp64(const double4* x4, int64_t N, double* phi, unsigned long long* counter,
+cudaError_t launch_exh_fp64(const double4_32a* x4, int64_t N, double* phi, unsigned long long* counter,
                             int* flags, int num_sms, cudaStream_t s);
 // Exact FP32-bulk Phi of sampled particles idx[0..n_idx) (out zeroed by the caller).
 cudaError_t launch_sampled_fp32(const float4* xhi, const float4* xlo, int64_t N,
