@@ -428,6 +428,8 @@ def main():
         line["tree"] = bench_tree(api, inputs, torch, dev, fp64["triples_per_s"], np)
         line["forces"] = bench_forces(api, inputs, torch, dev)
         line["serving"] = bench_serving(api, inputs, np)
+        # the same mix at an offered load the server keeps up with
+        line["serving_at_100_req_s"] = bench_serving(api, inputs, np, rate=100.0)
     if rank == 0 and not args.no_cpu_baseline:
         r, dt, m, nt = cpu_oracle_rate(X, 0)
         line["cpu_baseline"] = {"value": r, "unit": "triples/s", "cores": nt, "kind": "oracle",

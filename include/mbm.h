@@ -157,8 +157,9 @@ mbm_status mbm_potential_host(mbm_ctx* ctx, const double* X_host, int64_t N, dou
  * exhaustive sum is out of reach (cost: n_idx * C(N-1, 2) triples).
  *   idx_dev : n_idx int64 device indices in [0, N) (0 <= n_idx <= 2^20).
  *   out_dev : n_idx FP64 device array, written.
- * Indices are not range-checked on the device; out-of-range indices are
- * the caller's error. Asynchronous on `stream`.
+ * Indices outside [0, N) are skipped on the device (their output stays 0)
+ * and reported as MBM_EINVAL; non-finite coordinates likewise. Synchronises
+ * `stream` once at the end to read those flags.
  */
 mbm_status mbm_potential_sampled(mbm_ctx* ctx, const double* X_dev, int64_t N,
                                  const int64_t* idx_dev, int64_t n_idx, double* out_dev,

@@ -95,6 +95,7 @@ mbm_status mbm_check_flags(mbm_ctx* ctx, cudaStream_t stream) {
         return mbm_fail(MBM_EINVAL, "two particles coincide (phi is undefined at r = 0)");
     if (f & MBM_FLAG_OVERFLOW) return mbm_fail(MBM_EOVERFLOW, "device work list overflow");
     if (f & MBM_FLAG_TIMEOUT) return mbm_fail(MBM_ETIMEDOUT, "device wait timed out");
+    if (f & MBM_FLAG_INDEX) return mbm_fail(MBM_EINVAL, "particle index outside [0, N)");
     return MBM_OK;
 }
 
@@ -309,7 +310,8 @@ extern "C" mbm_status mbm_potential_sampled(mbm_ctx* ctx, const double* X_dev, i
     MBM_CUDA_TRY(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
     MBM_CUDA_TRY(launch_pack_hilo(X_dev, N, xh, xl, ctx->d_flags, s));
     mbm_time_begin(ctx, s);
-    MBM_CUDA_TRY(launch_sampled_fp32(xh, xl, N, idx_dev, n_idx, out_dev, ctx->num_sms, s));
+    MBM_CUDA_TRY(launch_sampled_fp32(xh, xl, N, idx_dev, n_idx, out_dev, ctx->d_flags,
+                                     ctx->num_sms, s));
     mbm_time_end(ctx, s);
-    return MBM_OK;
+    return mbm_check_flags(ctx, s);
 }

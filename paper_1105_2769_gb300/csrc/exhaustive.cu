@@ -289,7 +289,7 @@ constexpr int kSampleWarps = 4;
 __global__ void __launch_bounds__(kSampleWarps * 32, 1)
 sampled_fp32_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int N, int NT,
                     const int64_t* __restrict__ idx, int n_idx, double* __restrict__ out,
-                    long long n_items) {
+                    long long n_items, int* __restrict__ flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SampleWarpSmem& w = reinterpret_cast<SampleWarpSmem*>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -313,8 +313,11 @@ sampled_fp32_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl
         __syncwarp();
         for (int q0 = 0; q0 < n_idx; q0 += kTile) {
             const int q = q0 + lane;
-            const bool iv = q < n_idx;
-            const int64_t i = iv ? idx[q] : 0;
+            const int64_t i0 = q < n_idx ? idx[q] : 0;
+            const bool bad = q < n_idx && (i0 < 0 || i0 >= N);  // skipped and reported
+            if (bad && t == 0) atomicOr(flags, MBM_FLAG_INDEX);
+            const bool iv = q < n_idx && !bad;
+            const int64_t i = iv ? i0 : 0;
             const float4 ih = iv ? xh[i] : z4, il = iv ? xl[i] : z4;
             const float acc = mbm_tile::tile_triples(w.tab, w.sJh, w.sJl, w.sKh, w.sKl, ih, il, iv,
                                                      lane, nJ, nK, false, false, w.redJ, w.redK);
@@ -385,8 +388,8 @@ cudaError_t launch_exh_fp64(const double4_32a* x4, int64_t N, double* phi, unsig
 }
 
 cudaError_t launch_sampled_fp32(const float4* xhi, const float4* xlo, int64_t N,
-                                const int64_t* idx, int64_t n_idx, double* out, int num_sms,
-                                cudaStream_t s) {
+                                const int64_t* idx, int64_t n_idx, double* out, int* flags,
+                                int num_sms, cudaStream_t s) {
     const int NT = (int)((N + kTile - 1) / kTile);
     const long long items = (long long)NT * (NT + 1) / 2;
     const int threads = kSampleWarps * 32;
@@ -397,6 +400,6 @@ cudaError_t launch_sampled_fp32(const float4* xhi, const float4* xlo, int64_t N,
     const int grid = grid_for((const void*)sampled_fp32_kernel, threads, smem, num_sms,
                               (items + kSampleWarps - 1) / kSampleWarps);
     sampled_fp32_kernel<<<grid, threads, smem, s>>>(xhi, xlo, (int)N, NT, idx, (int)n_idx, out,
-                                                    items);
+                                                    items, flags);
     return cudaGetLastError();
 }

@@ -33,7 +33,8 @@ enum : int {
     MBM_FLAG_NONFINITE = 1,   // a coordinate is NaN or Inf
     MBM_FLAG_COINCIDENT = 2,  // two particles at zero distance
     MBM_FLAG_OVERFLOW = 4,    // a bounded work list overflowed
-    MBM_FLAG_TIMEOUT = 8      // a bounded device wait gave up
+    MBM_FLAG_TIMEOUT = 8,     // a bounded device wait gave up
+    MBM_FLAG_INDEX = 16       // a particle index outside [0, N)
 };
 
 // ---------------------------------------------------------------------------
@@ -89,5 +90,5 @@ cudaError_t launch_exh_fp64(const double4_32a* x4, int64_t N, double* phi, unsig
                             int* flags, int num_sms, cudaStream_t s);
 // Exact FP32-bulk Phi of sampled particles idx[0..n_idx) (out zeroed by the caller).
 cudaError_t launch_sampled_fp32(const float4* xhi, const float4* xlo, int64_t N,
-                                const int64_t* idx, int64_t n_idx, double* out, int num_sms,
-                                cudaStream_t s);
+                                const int64_t* idx, int64_t n_idx, double* out, int* flags,
+                                int num_sms, cudaStream_t s);

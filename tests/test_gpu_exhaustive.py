@@ -155,3 +155,24 @@ def test_sampled_exact_matches_oracle():
     # agrees with the full exhaustive FP32 solve on the same particles
     full = _gpu(X, "fp32")[idx]
     assert np.all(np.abs(got - full) <= TOL["fp32"] * ref_abs)
+
+
+def test_sampled_rejects_out_of_range_index_on_device():
+    """Indices are checked on the device too (the C entry point cannot trust
+    its caller): an index outside [0, N) is skipped and reported."""
+    import ctypes
+    X = torch.from_numpy(inputs.uniform_cube(200, 4.0, 0.5, 61)).cuda()
+    idx = torch.tensor([0, 5, 200, -1, 7], dtype=torch.int64, device="cuda")
+    out = torch.full((5,), 7.0, dtype=torch.float64, device="cuda")
+    ctx = api.default_context()
+    st = _lib.load().mbm_potential_sampled(ctx.handle, ctypes.c_void_p(X.data_ptr()), 200,
+                                           ctypes.c_void_p(idx.data_ptr()), 5,
+                                           ctypes.c_void_p(out.data_ptr()), None)
+    assert st == -1  # MBM_EINVAL
+    o = out.cpu().numpy()
+    assert o[2] == 0.0 and o[3] == 0.0
+    ref, ref_abs = oracle.phi(X.cpu().numpy(), np.array([0, 5, 7]), with_abs=True)
+    assert np.all(np.abs(o[[0, 1, 4]] - ref) <= TOL["fp32"] * ref_abs)
+    # the context stays usable
+    good = api.potential_sampled(X, [0, 5, 7]).cpu().numpy()
+    assert np.all(np.abs(good - o[[0, 1, 4]]) <= 1e-12 * ref_abs)
