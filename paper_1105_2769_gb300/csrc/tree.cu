@@ -307,7 +307,8 @@ seed_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_
 // is cut into pieces of at most kPiece items. A CTA takes a piece, builds the
 // (j,k) table of the pair once and its warps sweep the x leaves of the piece,
 // so the table and the (y, z) row sums are shared by up to kPiece leaf
-// triples. The arithmetic of every leaf triple is that of base_kernel.
+// triples. Every leaf triple runs the exhaustive tile routine with the Fig. 4
+// masks (x == y: i < j; y == z: j < k).
 constexpr int kBaseWarps = 4;
 constexpr int kPiece = 64;
 

@@ -8,8 +8,8 @@ for validity:
   * per-particle tuple counts of all prunes and base cases equal C(N-1, 2)
     exactly (integer invariant of the partition, Fig. 4);
   * deterministic rule: the same prunes as the serial restatement (Phi^l is
-    fixed before the traversal, so the breadth-first GPU order decides as the
-    depth-first recursion does), results equal to the FP32 bar, and the
+    fixed before the traversal, so the GPU's chunked level order decides as
+    the depth-first recursion does), results equal to the FP32 bar, and the
     guarantee of Sec. 5 (every particle within eps |Phi| + tau);
   * Monte Carlo rule: the same Philox draws as the restatement; sample phi is
     FP32 on the GPU and FP64 in the oracle, so a stop test within rounding of
