@@ -1097,10 +1097,10 @@ __device__ __forceinline__ void candidate_geometry(const Trav& p, const int64_t 
     }
 }
 
-// Probe: each distinct node's 8 particles with the smallest Phi^l(x) (the
-// likeliest to fail) run first; lanes 8s..8s+7 take slot s, a warp per
-// candidate. Decisions do not depend on this order.
-constexpr int kProbe = 8;
+// Probe: each distinct node's particles with the smallest Phi^l(x) (the
+// likeliest to fail) run first, a warp per candidate: 32, 16 or 10 of them
+// per node for 1, 2 or 3 distinct nodes, so the lanes are filled. A particle's
+// draws depend only on its own ids, so decisions do not depend on this order.
 __global__ void mc_probe_kernel(const int4* __restrict__ mc, int64_t n_c, int* cand_fail, Trav p) {
     const int lane = threadIdx.x & 31;
     const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -1112,11 +1112,14 @@ __global__ void mc_probe_kernel(const int4* __restrict__ mc, int64_t n_c, int* c
     bool first[3];
     int64_t bb[3], nn[3], U;
     candidate_geometry(p, P, T, first, bb, nn, U);
-    const int slot = lane / kProbe;
-    const bool mine = slot < 3 && first[slot];
-    const int x = mine ? p.weak[P[slot] * 32 + (lane % kProbe)] : -1;
-    mc_warp(p, P, bb, nn, x >= 0, slot < 3 ? slot : 0, x >= 0 ? x : 0, slot < 3 ? T[slot] : 0.0,
-            fail);
+    int ds[3], d = 0;  // distinct slots in order
+    for (int s = 0; s < 3; ++s)
+        if (first[s]) ds[d++] = s;
+    const int per = d == 1 ? 32 : (d == 2 ? 16 : 10);
+    const int q = lane / per;
+    const int slot = q < d ? ds[q] : 0;
+    const int x = q < d ? p.weak[P[slot] * 32 + (lane % per)] : -1;
+    mc_warp(p, P, bb, nn, x >= 0, slot, x >= 0 ? x : 0, T[slot], fail);
 }
 
 __global__ void mc_sizes_kernel(const int4* __restrict__ mc, int64_t n_mc, int64_t N,
