@@ -1313,7 +1313,7 @@ TravPlan trav_plan(int64_t N, int depth, int m_limit, bool counting) {
     const int64_t n_nodes = ((int64_t)2 << depth) - 1, n_leaves = (int64_t)1 << depth;
     // Frontier chunk B: a chunk of B node triples yields at most 4B children,
     // B Monte Carlo candidates and B base cases, so no list can overflow.
-    q.B = std::max<int64_t>(1 << 14, std::min<int64_t>(1 << 20, 2 * N));
+    q.B = std::max<int64_t>(1 << 14, std::min<int64_t>(1 << 20, 16 * N));
     q.max_levels = 3 * depth + 8;
     q.cap_lvl = 4 * q.B;
     q.cap_mc = q.B;
