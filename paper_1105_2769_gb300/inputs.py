@@ -199,6 +199,8 @@ def workload(name: str, return_stats: bool = False):
                       per-component structure match the 2^20 set; seed 3
     gmm16_n262144   : the same with 16 components (262 144 points) in a cube
                       of side 100 (16/64)^(1/3); seed 3
+    gmm32_n524288   : the same with 32 components (524 288 points) in a cube
+                      of side 100 (32/64)^(1/3); seed 3
     """
     if name == "exh64_n512":
         r = uniform_cube(512, 1.0, 0.01, 1, return_stats=True)
@@ -213,6 +215,9 @@ def workload(name: str, return_stats: bool = False):
                              return_stats=True)
     elif name == "gmm16_n262144":
         r = gaussian_mixture(1 << 18, 16, 100.0 * (16 / 64) ** (1 / 3), 0.5, 3.0, 0.05, 3,
+                             return_stats=True)
+    elif name == "gmm32_n524288":
+        r = gaussian_mixture(1 << 19, 32, 100.0 * (32 / 64) ** (1 / 3), 0.5, 3.0, 0.05, 3,
                              return_stats=True)
     else:
         raise KeyError(name)
