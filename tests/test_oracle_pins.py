@@ -181,3 +181,85 @@ def test_subset_matches_full(oracle_lib):
     full = oracle_lib.phi(X)
     idx = np.array([0, 5, 79, 40])
     np.testing.assert_array_equal(oracle_lib.phi(X, idx), full[idx])
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes: each mutant below is a copy of the oracle's phi source
+# with one plausible slip, compiled on its own; the pins above must reject
+# every one of them (and accept the unmodified copy).
+# ---------------------------------------------------------------------------
+_MUTANTS = {
+    "control": None,
+    "sign of the cosine term": ("return (1.0 + 3.0 * ci * cj * ck) / den;",
+                                "return (1.0 - 3.0 * ci * cj * ck) / den;"),
+    "dropped factor 3": ("return (1.0 + 3.0 * ci * cj * ck) / den;",
+                         "return (1.0 + ci * cj * ck) / den;"),
+    "wrong power of r_ij": ("double den = rij * rij * rij * rik",
+                            "double den = rij * rij * rik"),
+    "wrong vertex vector for cos t_j": ("double cj = dot3(eji, ejk) / (rij * rjk);",
+                                        "double cj = dot3(eij, ejk) / (rij * rjk);"),
+    "transposed length in cos t_k": ("double ck = dot3(eki, ekj) / (rik * rjk);",
+                                     "double ck = dot3(eki, ekj) / (rik * rij);"),
+    "ordered pairs counted twice": ("for (int64_t k = j + 1; k < N; ++k) {\n                if (k == i) continue;\n                double p = oracle_at_phi",
+                                    "for (int64_t k = 0; k < N; ++k) {\n                if (k == i || k == j) continue;\n                double p = oracle_at_phi"),
+}
+
+
+def _build_mutant(tmp_path, name, edit):
+    import ctypes
+    import subprocess
+    src = open(os.path.join(os.path.dirname(GOLDEN), "..", "oracle", "at_oracle.c")).read()
+    if edit is not None:
+        assert src.count(edit[0]) == 1, name
+        src = src.replace(edit[0], edit[1])
+    c = tmp_path / f"m{abs(hash(name))}.c"
+    so = tmp_path / f"m{abs(hash(name))}.so"
+    c.write_text(src)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                    "-o", str(so), str(c), "-lm"], check=True)
+    L = ctypes.CDLL(str(so))
+    dp, i64, ip = (ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                   ctypes.POINTER(ctypes.c_int64))
+    L.oracle_at_phi.restype = ctypes.c_double
+    L.oracle_at_phi.argtypes = [dp, dp, dp]
+    L.oracle_phi.argtypes = [dp, i64, ip, i64, dp, dp, ctypes.c_int]
+
+    def at_phi(a, b, c3):
+        a, b, c3 = (np.ascontiguousarray(v, dtype=np.float64) for v in (a, b, c3))
+        return L.oracle_at_phi(*(v.ctypes.data_as(dp) for v in (a, b, c3)))
+
+    def phi(X):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        idx = np.arange(len(X), dtype=np.int64)
+        out = np.zeros(len(X))
+        assert L.oracle_phi(X.ctypes.data_as(dp), len(X), idx.ctypes.data_as(ip), len(X),
+                            out.ctypes.data_as(dp), None, 1) == 0
+        return out
+
+    return at_phi, phi
+
+
+def _pins_hold(at_phi, phi):
+    """The closed forms, the tetrahedron and the decimal brute force, as booleans."""
+    def close(a, b):
+        a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
+        return bool(np.all(np.isfinite(a)) and np.allclose(a, b, rtol=1e-12, atol=0))
+    for _name, pts, expected, _why in _read_fixture("closed_forms.txt"):
+        P = np.array([[float(v) for v in p.split()] for p in pts.split(";")])
+        if not (close(at_phi(P[0], P[1], P[2]), float(expected)) and
+                close(phi(P), float(expected))):
+            return False
+    T = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=np.float64)
+    if not close(phi(T), [float(r[1]) for r in _read_fixture("tetrahedron.txt")]):
+        return False
+    X = inputs.uniform_cube(6, 1.0, 0.05, 31)
+    return close(phi(X), _decimal_phi_all(X))
+
+
+@pytest.mark.parametrize("name", list(_MUTANTS))
+def test_pins_reject_planted_mistakes(tmp_path, name):
+    at_phi, phi = _build_mutant(tmp_path, name, _MUTANTS[name])
+    if name == "control":
+        assert _pins_hold(at_phi, phi)
+    else:
+        assert not _pins_hold(at_phi, phi), f"the pins did not catch: {name}"

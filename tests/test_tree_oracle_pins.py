@@ -127,3 +127,81 @@ def test_mc_is_deterministic_in_seed(gmm):
     c, _, sc = tree.tree_potential(X, eps=0.1, alpha=0.05, seed=8, zeta=4.0)
     assert np.array_equal(a, b) and sa == sb
     assert sc["mc_samples"] != sa["mc_samples"] or not np.array_equal(a, c)
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes in the tree restatement: each mutant is a copy of the
+# oracle with one plausible slip (a Fig. 4 count, the budget's T^root),
+# compiled on its own; the pins (exact at eps = 0, tuple counts = C(N-1, 2),
+# the deterministic, absolute and Monte Carlo guarantees) must reject every
+# one of them and accept the unmodified copy. The value a prune credits is
+# not among them: with T^root in the budget every pruned contribution on
+# these sets is far below the allowed error (a copy that drops them all, or
+# credits them all to the first node, still meets eps and tau), so that part
+# is checked by the agreement of the two independent implementations (GPU vs
+# oracle to 3e-6 sum|phi| per particle, while such a slip moves Phi by
+# ~1e-4 |Phi|).
+# ---------------------------------------------------------------------------
+_TREE_MUTANTS = {
+    "control": None,
+    "Fig. 4 case (b) count": ("(n[0] - 1.0) * n[2];     /* (b) */", "n[0] * n[2];     /* (b) */"),
+    "Fig. 4 case (c) count": ("n[0] * (n[1] - 1.0);     /* (c) */", "n[0] * n[1];     /* (c) */"),
+    "Fig. 4 case (d) slot": ("if (slot == 0) return n[1] * n[2];", "if (slot == 0) return n[0] * n[2];"),
+    "budget without T^root": ("+ S->tau) / S->troot;", "+ S->tau);"),
+}
+
+
+def _tree_mutant(tmp_path, name, edit):
+    import ctypes
+    import os
+    import subprocess
+    here = os.path.dirname(oracle.__file__)
+    src = open(os.path.join(here, "tree_oracle.c")).read()
+    if edit is not None:
+        assert src.count(edit[0]) == 1, name
+        src = src.replace(edit[0], edit[1])
+    tag = f"t{abs(hash(name))}"
+    c = tmp_path / f"{tag}.c"
+    so = tmp_path / f"{tag}.so"
+    c.write_text(src)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                    "-o", str(so), str(c), os.path.join(here, "at_oracle.c"), "-lm"], check=True)
+    L = ctypes.CDLL(str(so))
+    i64, dbl, vp = ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    L.oracle_tree_potential.argtypes = [vp, i64, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int, dbl,
+                                        ctypes.c_uint64, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+
+    def solve(X, eps, tau=0.0, alpha=0.0, zeta=32.0):
+        out = np.zeros(len(X))
+        cnt = np.zeros(len(X), dtype=np.int64)
+        st = np.zeros(6, dtype=np.int64)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        assert L.oracle_tree_potential(p(X), len(X), eps, tau, alpha, 8, 256, zeta, 1, 0, 3,
+                                       p(out), p(cnt), p(st)) == 0
+        return out, cnt, st
+    return solve
+
+
+@pytest.mark.parametrize("name", list(_TREE_MUTANTS))
+def test_tree_pins_reject_planted_mistakes(tmp_path, name):
+    X = np.ascontiguousarray(inputs.gaussian_mixture(600, 4, 8.0, 0.5, 1.5, 0.05, 5))
+    ex = oracle.phi(X)
+    solve = _tree_mutant(tmp_path, name, _TREE_MUTANTS[name])
+    T = comb(len(X) - 1, 2)
+    checks = []
+    phi, cnt, _ = solve(X, 0.0)                              # exact, partition
+    checks += [np.allclose(phi, ex, rtol=1e-12, atol=0), np.all(cnt == T)]
+    phi, cnt, st = solve(X, 0.1)                             # deterministic guarantee
+    checks += [np.all(cnt == T), np.all(np.abs(phi - ex) <= 0.1 * np.abs(ex))]
+    tau = 1e-3 * float(np.median(np.abs(ex)))                # absolute rule
+    phi, cnt, st = solve(X, 0.0, tau=tau)
+    checks += [st[1] > 0, np.all(cnt == T), np.all(np.abs(phi - ex) <= tau)]
+    phi, cnt, st = solve(X, 0.1, alpha=0.05, zeta=4.0)       # Monte Carlo, partition
+    within = np.abs(phi - ex) <= 0.1 * np.abs(ex)
+    checks += [st[2] > 0, np.all(cnt == T),
+               within.mean() >= 0.95 - 3.0 * np.sqrt(0.05 * 0.95 / len(X))]
+    holds = all(bool(c) for c in checks)
+    if name == "control":
+        assert holds
+    else:
+        assert not holds, f"the pins did not catch: {name}"
