@@ -947,10 +947,11 @@ __device__ __forceinline__ mbm_tile::PairF pair_sample(float4 ph, float4 pl, flo
     return r;
 }
 
-// phi of one point triple in FP32 bulk (direction-cosine form).
-__device__ __forceinline__ float phi_fp32(const float4* xh, const float4* xl, int64_t a, int64_t b,
-                                          int64_t c) {
-    const float4 ah = xh[a], al = xl[a], bh = xh[b], bl = xl[b], ch = xh[c], cl = xl[c];
+// phi of one point triple in FP32 bulk (direction-cosine form); the first
+// point is given (hi/lo), the other two are loaded.
+__device__ __forceinline__ float phi_fp32(float4 ah, float4 al, const float4* xh, const float4* xl,
+                                          int64_t b, int64_t c) {
+    const float4 bh = xh[b], bl = xl[b], ch = xh[c], cl = xl[c];
     const mbm_tile::PairF ab = pair_sample(ah, al, bh, bl);
     const mbm_tile::PairF ac = pair_sample(ah, al, ch, cl);
     const mbm_tile::PairF bc = pair_sample(bh, bl, ch, cl);
@@ -1010,69 +1011,78 @@ __device__ double mc_warp(const Trav& p, const int64_t P[3], const int64_t bb[3]
     int m = 0, next_test = 30;
     bool pass = false, done = !active;
     int samples = 0, iter = 0;
-    uint32_t rr[4] = {0, 0, 0, 0};
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 xh0 = active ? p.xh[x] : z4, xl0 = active ? p.xl[x] : z4;
+    // One sample: Welford update and the stop test of Algorithm 4 at count m.
+    auto step = [&](double f) {
+        ++m;
+        ++samples;
+        // Welford updates of the running mean and sum of squares (fused)
+        const double dlt = __dsub_rn(f, mean);
+        mean = __fma_rn(dlt, p.rcp[m], mean);
+        m2 = __fma_rn(dlt, __dsub_rn(f, mean), m2);
+        // Tests before next_test are skipped: each would fail the
+        // variance comparison below (m2 never decreases).
+        const bool testing = m >= 2 && ((m >= 30 && m >= next_test) || m >= p.m_limit);
+        const double var_mu = testing ? __dmul_rn(__dmul_rn(m2, p.rcp[m - 1]), p.rcp[m]) : 0.0;
+        if (m >= 2 && m2 > hopeless_m2 &&
+            m2 > hopeless_m2 + 1e-20 * mean * mean) {  // no later m can pass
+            pass = false;
+            done = true;
+        } else if (testing && var_mu > reject_v) {  // cannot pass at this m
+            pass = false;
+            if (m >= p.m_limit) {
+                done = true;
+            } else if (reject_v > 0.0) {
+                // The first m' that can pass has (m'-1) m' >= m2 / reject_v; the
+                // root is taken in FP32 from a bound shrunk by 1e-4 (and by the
+                // rounding slack of m2), so every skipped m' would fail here.
+                const float K =
+                    (float)((m2 - 1e-20 * mean * mean) / reject_v) * 0.9999f;
+                if (K > 0.0f) {
+                    const float root = 0.5f * (1.0f + sqrtf(fmaf(4.0f, K, 1.0f)));
+                    const int nt = root < (float)p.m_limit ? (int)root : p.m_limit;
+                    if (nt > next_test) next_test = nt;
+                }
+            }
+        } else if (testing) {  // the test can end the loop only here
+            // sigma_mu = sqrt(m2 / (m-1) / m), with exact reciprocals
+            const double sig = __dsqrt_rn(var_mu);
+            const double lhs = __dmul_rn(p.z, sig);
+            double lb = __dsub_rn(phil, __dmul_rn(Ti, __dadd_rn(fabs(mean), __dmul_rn(p.z, sig))));
+            if (lb < 0.0) lb = 0.0;
+            const double rhs =
+                p.mc_rule == 1
+                    ? __dmul_rn(__dadd_rn(__ddiv_rn(__dmul_rn(p.eps, lb), Ti), p.tau), p.inv_troot)
+                    : __dmul_rn(__dadd_rn(__dmul_rn(p.eps, lb), p.tau), p.inv_troot);
+            pass = lhs <= rhs;
+            if ((pass && m >= 30) || m >= p.m_limit) done = true;
+        } else if (m >= p.m_limit) {  // m_limit < 2
+            pass = false;
+            done = true;
+        }
+        if (done && !pass) *fail = 1;
+    };
     while (__any_sync(0xffffffffu, !done)) {
         if (!done) {
-            // one Philox call serves samples 2c and 2c+1 (words 0,1 and 2,3)
-            if ((m & 1) == 0) {
-                const int c = m >> 1;
-                const uint32_t ctr1 = (uint32_t)P[0] | ((uint32_t)(c & 0xFF) << 24);
-                const uint32_t ctr2 = (uint32_t)P[1] | ((uint32_t)((c >> 8) & 0xFF) << 24);
-                philox4x32_10((uint32_t)x, ctr1, ctr2, (uint32_t)P[2], p.key0, p.key1, rr);
-            }
-            const uint32_t ra = (m & 1) ? rr[2] : rr[0], rb = (m & 1) ? rr[3] : rr[1];
-            int64_t y, zz;
-            draw_partners(P, bb, nn, slot, x, ra, rb, y, zz);
-            const double f = (double)phi_fp32(p.xh, p.xl, x, y, zz);
-            ++m;
-            ++samples;
-            // Welford updates of the running mean and sum of squares (fused)
-            const double dlt = __dsub_rn(f, mean);
-            mean = __fma_rn(dlt, p.rcp[m], mean);
-            m2 = __fma_rn(dlt, __dsub_rn(f, mean), m2);
-            // Tests before next_test are skipped: each would fail the
-            // variance comparison below (m2 never decreases).
-            const bool testing = m >= 2 && ((m >= 30 && m >= next_test) || m >= p.m_limit);
-            const double var_mu = testing ? __dmul_rn(__dmul_rn(m2, p.rcp[m - 1]), p.rcp[m]) : 0.0;
-            if (m >= 2 && m2 > hopeless_m2 &&
-                m2 > hopeless_m2 + 1e-20 * mean * mean) {  // no later m can pass
-                pass = false;
-                done = true;
-            } else if (testing && var_mu > reject_v) {  // cannot pass at this m
-                pass = false;
-                if (m >= p.m_limit) {
-                    done = true;
-                } else if (reject_v > 0.0) {
-                    // The first m' that can pass has (m'-1) m' >= m2 / reject_v; the
-                    // root is taken in FP32 from a bound shrunk by 1e-4 (and by the
-                    // rounding slack of m2), so every skipped m' would fail here.
-                    const float K =
-                        (float)((m2 - 1e-20 * mean * mean) / reject_v) * 0.9999f;
-                    if (K > 0.0f) {
-                        const float root = 0.5f * (1.0f + sqrtf(fmaf(4.0f, K, 1.0f)));
-                        const int nt = root < (float)p.m_limit ? (int)root : p.m_limit;
-                        if (nt > next_test) next_test = nt;
-                    }
-                }
-            } else if (testing) {  // the test can end the loop only here
-                // sigma_mu = sqrt(m2 / (m-1) / m), with exact reciprocals
-                const double sig = __dsqrt_rn(var_mu);
-                const double lhs = __dmul_rn(p.z, sig);
-                double lb = __dsub_rn(phil, __dmul_rn(Ti, __dadd_rn(fabs(mean), __dmul_rn(p.z, sig))));
-                if (lb < 0.0) lb = 0.0;
-                const double rhs =
-                    p.mc_rule == 1
-                        ? __dmul_rn(__dadd_rn(__ddiv_rn(__dmul_rn(p.eps, lb), Ti), p.tau), p.inv_troot)
-                        : __dmul_rn(__dadd_rn(__dmul_rn(p.eps, lb), p.tau), p.inv_troot);
-                pass = lhs <= rhs;
-                if ((pass && m >= 30) || m >= p.m_limit) done = true;
-            } else if (m >= p.m_limit) {  // m_limit < 2
-                pass = false;
-                done = true;
-            }
-            if (done && !pass) *fail = 1;
+            // One Philox call serves samples m and m+1 (m even; words 0,1 and
+            // 2,3). Both are drawn and evaluated before either is used, so
+            // their point loads overlap; they are then taken in order, and the
+            // second is dropped if the first ends the loop.
+            const int c = m >> 1;
+            const uint32_t ctr1 = (uint32_t)P[0] | ((uint32_t)(c & 0xFF) << 24);
+            const uint32_t ctr2 = (uint32_t)P[1] | ((uint32_t)((c >> 8) & 0xFF) << 24);
+            uint32_t rr[4];
+            philox4x32_10((uint32_t)x, ctr1, ctr2, (uint32_t)P[2], p.key0, p.key1, rr);
+            int64_t y0, z0, y1, z1;
+            draw_partners(P, bb, nn, slot, x, rr[0], rr[1], y0, z0);
+            draw_partners(P, bb, nn, slot, x, rr[2], rr[3], y1, z1);
+            const float f0 = phi_fp32(xh0, xl0, p.xh, p.xl, y0, z0);
+            const float f1 = phi_fp32(xh0, xl0, p.xh, p.xl, y1, z1);
+            step((double)f0);
+            if (!done) step((double)f1);
         }
-        if ((++iter & 31) == 0) {  // another particle already failed: stop the warp
+        if ((++iter & 15) == 0) {  // another particle already failed: stop the warp
             int f = lane == 0 ? *fail : 0;
             if (__shfl_sync(0xffffffffu, f, 0)) break;
         }
