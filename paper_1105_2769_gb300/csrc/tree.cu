@@ -1784,7 +1784,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
                 int64_t c1 = c0 + 1;
                 while (c1 < n_mc && (off[c1 + 1] - off[c0]) * 32 <= cap_est) ++c1;
                 const int64_t chunks = off[c1] - off[c0];
-                mc_kernel<<<grid_of(chunks * 32, 256), 256, 0, s>>>(mcl + c0, 0, c1 - c0,
+                mc_kernel<<<grid_of(chunks * 32, 128), 128, 0, s>>>(mcl + c0, 0, c1 - c0,
                                                                     chunk_off + c0, cand_fail + c0,
                                                                     est, p);
                 mc_commit_kernel<<<(unsigned)(c1 - c0), 256, 0, s>>>(
