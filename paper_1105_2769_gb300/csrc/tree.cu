@@ -19,8 +19,9 @@
 //   a7 Monte Carlo  : Algorithms 3-5; a lane per particle draws tuples with
 //                     Philox-4x32-10, FP32 phi, FP64 Welford statistics and
 //                     stop test; a triple passes only if all its particles do,
-//                     so each candidate first tests its 8 weakest particles
-//                     (smallest Phi^l) per node and stops at the first failure.
+//                     so each candidate first tests its weakest particles
+//                     (smallest Phi^l; 32, 16 or 10 per node for 1, 2 or 3
+//                     distinct nodes) and stops at the first failure.
 //   a8 base cases   : exhaustive leaf triples with the Fig. 4 masks, FP32 bulk
 //                     (tile_fp32.cuh), FP64 accumulation; each flush of the
 //                     base list is sorted by (y, z) leaf pair so a CTA shares
