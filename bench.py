@@ -296,6 +296,46 @@ def bench_serving(api, inputs, np, duration=6.0, rate=200.0):
             "mix": "70% tree Phi (eps 1e-2, alpha 0.05, resident systems), 30% FP32 forces"}
 
 
+def run_paper_shape(args):
+    """The paper's experiment shapes (Sec. 6) on this GPU: uniform cube, unit
+    ball and thin shell ("annulus"), tree solves at eps 1e-1/1e-2/1e-3 and
+    alpha 0 / 0.1, against the FP64 exhaustive solve of the same set: speed-up
+    and the fraction of particles within eps (the statistics of Tables 1-3)."""
+    import numpy as np
+    import torch
+
+    from paper_1105_2769_gb300 import api, inputs
+    dev = torch.device("cuda", 0)
+    sets = {"uniform": lambda n: inputs.uniform_cube(n, 1.0, 1e-3, 41),
+            "ball": lambda n: inputs.unit_ball(n, 1e-3, 42),
+            "shell": lambda n: inputs.spherical_shell(n, 0.95, 1.0, 1e-3, 43)}
+    rows = []
+    for name, gen in sets.items():
+        for n in (2000, 10000):
+            X = gen(n)
+            Xd = torch.from_numpy(X).to(dev)
+            api.potential(Xd, mode="fp64")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ex = api.potential(Xd, mode="fp64").cpu().numpy()
+            t_ex = time.perf_counter() - t0
+            for eps in (1e-1, 1e-2, 1e-3):
+                for alpha in (0.0, 0.1):
+                    api.potential(Xd, eps=eps, alpha=alpha, mode="tree")
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    phi = api.potential(Xd, eps=eps, alpha=alpha, mode="tree").cpu().numpy()
+                    dt = time.perf_counter() - t0
+                    rel = np.abs(phi - ex) / np.abs(ex)
+                    rows.append({"set": name, "n": n, "eps": eps, "alpha": alpha,
+                                 "tree_s": dt, "fp64_exhaustive_s": t_ex,
+                                 "speedup": t_ex / dt, "within_eps": float(np.mean(rel <= eps)),
+                                 "mean_rel_err": float(rel.mean()), "max_rel_err": float(rel.max())})
+                    print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"report": "paper_shape", "rows": len(rows)}))
+    return 0
+
+
 def run_tree_only(args):
     import numpy as np
     import torch
@@ -324,11 +364,15 @@ def main():
                          "solve per eps without warm-up, and print their JSON report")
     ap.add_argument("--tree-eps", default="1e-2,1e-1")
     ap.add_argument("--tree-sample", type=int, default=256)
+    ap.add_argument("--paper-shape", action="store_true",
+                    help="tree vs FP64 exhaustive on the paper's uniform/ball/shell shapes")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.tree_only:
         return run_tree_only(args)
+    if args.paper_shape:
+        return run_paper_shape(args)
 
     import numpy as np
     import torch

@@ -154,3 +154,18 @@ def test_bad_arguments(gmm):
         api.potential(Xd, eps=0.1, mode="tree", config=api.tree_config(leaf_size=64))
     with pytest.raises(_lib.MbmError):
         api.potential(Xd, eps=0.1, mode="tree", config=api.tree_config(seed_levels=8))
+
+
+def test_hybrid_rule(gmm):
+    """Relative eps and absolute tau together (the hybrid rule of Sec. 4):
+    the same prunes as the restatement, the partition, and every particle
+    within eps |Phi| + tau."""
+    X, ex, ab = gmm
+    tau = 1e-3 * float(np.median(np.abs(ex)))
+    eps = 0.01
+    phi, cnt, st = _gpu_tree(X, eps, 0.0, tau=tau)
+    assert np.all(cnt == comb(len(X) - 1, 2))
+    assert st["det_prunes"] > 0
+    assert np.all(np.abs(phi - ex) <= eps * np.abs(ex) + tau + FP32_BAR * ab)
+    ref, _, rst = otree.tree_potential(X, eps=eps, tau=tau, alpha=0.0, with_counts=True)
+    assert st["det_prunes"] == rst["det_prunes"]
