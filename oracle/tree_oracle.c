@@ -36,7 +36,11 @@
  *
  * Parity status: pinned by the exact-result special case eps = tau = 0, the
  * per-point tuple-count partition invariant, brute force of the interval
- * bound, the guarantees of Sec. 5 and Philox known-answer vectors.
+ * bound, the guarantees of Sec. 5 and Philox known-answer vectors; the
+ * credited values (Summarize, Algorithm 5), the Monte Carlo partner draws
+ * and the top-down push by an exact rebuild of the result from the record
+ * of prunes (oracle_tree_potential_trace) and by uniformity of the draws
+ * over the valid tuples (oracle_mc_draw).
  */
 #include <math.h>
 #include <stdint.h>
@@ -182,6 +186,23 @@ static void tree_free(otree* t) {
 static inline int64_t node_n(const otree* t, int64_t v) { return t->end[v] - t->begin[v]; }
 static inline int is_leaf(const otree* t, int64_t v) { return v >= t->n_nodes - t->n_leaves; }
 
+/* ---------------- decision trace (for the tests' credit pins) ----------------
+ * Caller-provided buffers; a full buffer keeps counting but stops writing.
+ *   tri   : 4 int64 per prune: kind (0 = deterministic, 1 = Monte Carlo), P1, P2, P3
+ *   mc_*  : one entry per point of a Monte Carlo prune: prune number (index
+ *           into tri), sorted point index, sample mean mu, sigma_mu, samples
+ */
+typedef struct {
+    int64_t cap_tri, n_tri;
+    int64_t* tri;
+    int64_t cap_mc, n_mc;
+    int64_t* mc_tri;
+    int64_t* mc_pt;
+    double* mc_mean;
+    double* mc_sig;
+    int64_t* mc_m;
+} otrace;
+
 /* ---------------- state of one solve ---------------- */
 typedef struct {
     const otree* t;
@@ -194,7 +215,19 @@ typedef struct {
     int64_t* node_cnt;  /* tuple counts (invariant check) */
     int64_t* pt_cnt;
     int64_t det_prunes, mc_prunes, mc_attempts, base_cases, visited, mc_samples;
+    otrace* trace;      /* optional */
 } osolve;
+
+static int64_t trace_prune(osolve* S, int kind, const int64_t P[3]) {
+    otrace* tr = S->trace;
+    if (!tr) return -1;
+    int64_t k = tr->n_tri++;
+    if (k < tr->cap_tri) {
+        tr->tri[4 * k] = kind;
+        for (int s = 0; s < 3; ++s) tr->tri[4 * k + 1 + s] = P[s];
+    }
+    return k;
+}
 
 static double choose2(double n) { return n * (n - 1.0) * 0.5; }
 
@@ -331,12 +364,14 @@ static void draw_partners(const osolve* S, const int64_t P[3], int slot, int64_t
 }
 
 /* Algorithm 4 for point x (sorted index) of slot `slot`; returns 1 if the
- * point passes, and its estimate T_i * mu in *est. */
+ * point passes, and its estimate T_i * mu in *est (mu, sigma_mu and the
+ * number of samples in mus[0..2]). */
 static int mc_point(osolve* S, const int64_t P[3], int slot, int64_t x, double Ti, double phil,
-                    double* est) {
+                    double* est, double mus[3]) {
     const otree* t = S->t;
     double mean = 0.0, m2 = 0.0;
     int m = 0, pass = 0;
+    double sig = 0.0;
     uint32_t r[4] = {0, 0, 0, 0};
     for (;;) {
         /* one Philox call per two samples: sample m uses words 2(m%2), 2(m%2)+1
@@ -356,7 +391,7 @@ static int mc_point(osolve* S, const int64_t P[3], int slot, int64_t x, double T
         m2 += dlt * (f - mean);                          /* running sum of squares */
         if (m >= 2 && (m >= 30 || m >= S->m_limit)) { /* the loop can only end here */
             /* sigma_mu = s / sqrt(m), s^2 = m2 / (m - 1) (sample variance with m-1) */
-            double sig = sqrt(m2 * (1.0 / (double)(m - 1)) * (1.0 / (double)m));
+            sig = sqrt(m2 * (1.0 / (double)(m - 1)) * (1.0 / (double)m));
             double lhs = S->z * sig, rhs;
             double lb = phil - Ti * (fabs(mean) + S->z * sig);
             if (lb < 0.0) lb = 0.0;
@@ -373,6 +408,9 @@ static int mc_point(osolve* S, const int64_t P[3], int slot, int64_t x, double T
     }
     S->mc_samples += m;
     *est = Ti * mean;
+    mus[0] = mean;
+    mus[1] = sig;
+    mus[2] = (double)m;
     return pass;
 }
 
@@ -432,6 +470,7 @@ static int try_summarize(osolve* S, const int64_t P[3]) {
             if (S->node_cnt) S->node_cnt[P[s]] += (int64_t)T[s];
         }
         S->det_prunes++;
+        trace_prune(S, 0, P);
         return 1;
     }
     /* ---- Monte Carlo rule (Algorithm 3) ---- */
@@ -443,19 +482,36 @@ static int try_summarize(osolve* S, const int64_t P[3]) {
             int64_t total = 0;
             for (int s = 0; s < 3; ++s) if (first[s]) total += node_n(t, P[s]);
             double* est = (double*)malloc(sizeof(double) * (size_t)total);
+            double* mus = (double*)malloc(sizeof(double) * 3 * (size_t)total);
             int64_t q = 0;
             int ok = 1;
             for (int s = 0; s < 3 && ok; ++s) {
                 if (!first[s]) continue;
                 for (int64_t x = t->begin[P[s]]; x < t->end[P[s]]; ++x) {
-                    if (!mc_point(S, P, s, x, T[s], t->pphil[x], &est[q++])) { ok = 0; break; }
+                    if (!mc_point(S, P, s, x, T[s], t->pphil[x], &est[q], mus + 3 * q)) {
+                        ok = 0;
+                        break;
+                    }
+                    ++q;
                 }
             }
             if (ok) { /* Algorithm 5 */
+                int64_t k = trace_prune(S, 1, P);
                 q = 0;
                 for (int s = 0; s < 3; ++s) {
                     if (!first[s]) continue;
                     for (int64_t x = t->begin[P[s]]; x < t->end[P[s]]; ++x) {
+                        if (S->trace) {
+                            otrace* tr = S->trace;
+                            int64_t e = tr->n_mc++;
+                            if (e < tr->cap_mc) {
+                                tr->mc_tri[e] = k;
+                                tr->mc_pt[e] = x;
+                                tr->mc_mean[e] = mus[3 * q];
+                                tr->mc_sig[e] = mus[3 * q + 1];
+                                tr->mc_m[e] = (int64_t)mus[3 * q + 2];
+                            }
+                        }
                         pt_add(S, x, est[q++]);
                         if (S->pt_cnt) S->pt_cnt[x] += (int64_t)T[s];
                     }
@@ -463,6 +519,7 @@ static int try_summarize(osolve* S, const int64_t P[3]) {
                 S->mc_prunes++;
             }
             free(est);
+            free(mus);
             if (ok) return 1;
         }
     }
@@ -534,9 +591,10 @@ static void seed_phil(otree* t, int seed_up) {
  *   stats (optional, int64[6]): visited, det prunes, MC prunes, MC attempts,
  *   base cases, MC samples.
  */
-int oracle_tree_potential(const double* X, int64_t N, double eps, double tau, double alpha,
+static int tree_potential(const double* X, int64_t N, double eps, double tau, double alpha,
                           int leaf_size, int m_limit, double zeta, uint64_t seed, int mc_rule,
-                          int seed_up, double* out, int64_t* counts, int64_t* stats) {
+                          int seed_up, double* out, int64_t* counts, int64_t* stats,
+                          otrace* trace) {
     if (N < 3) {
         for (int64_t i = 0; i < N; ++i) { out[i] = 0.0; if (counts) counts[i] = 0; }
         return 0;
@@ -549,6 +607,7 @@ int oracle_tree_potential(const double* X, int64_t N, double eps, double tau, do
     S.t = &t;
     S.eps = eps; S.tau = tau; S.alpha = alpha; S.zeta = zeta;
     S.m_limit = m_limit; S.mc_rule = mc_rule;
+    S.trace = trace;
     S.troot = choose2((double)(N - 1));
     S.z = oracle_z_two_sided(alpha);
     S.key[0] = (uint32_t)seed; S.key[1] = (uint32_t)(seed >> 32);
@@ -581,6 +640,62 @@ int oracle_tree_potential(const double* X, int64_t N, double eps, double tau, do
     free(S.node_acc); free(S.pt_acc); free(S.pt_cmp);
     if (counts) { free(S.node_cnt); free(S.pt_cnt); }
     tree_free(&t);
+    return 0;
+}
+
+int oracle_tree_potential(const double* X, int64_t N, double eps, double tau, double alpha,
+                          int leaf_size, int m_limit, double zeta, uint64_t seed, int mc_rule,
+                          int seed_up, double* out, int64_t* counts, int64_t* stats) {
+    return tree_potential(X, N, eps, tau, alpha, leaf_size, m_limit, zeta, seed, mc_rule, seed_up,
+                          out, counts, stats, NULL);
+}
+
+/* The same solve, recording every prune (see otrace) into caller buffers:
+ * tri (4 x cap_tri int64), and per Monte Carlo point mc_tri, mc_pt, mc_m
+ * (int64) and mc_mean, mc_sig (double), cap_mc entries each. n_out[0..1]
+ * receive the number of prunes and of Monte Carlo point entries (which may
+ * exceed the capacities; entries past them are not written). */
+int oracle_tree_potential_trace(const double* X, int64_t N, double eps, double tau, double alpha,
+                                int leaf_size, int m_limit, double zeta, uint64_t seed,
+                                int mc_rule, int seed_up, double* out, int64_t* stats,
+                                int64_t* tri, int64_t cap_tri, int64_t* mc_tri, int64_t* mc_pt,
+                                double* mc_mean, double* mc_sig, int64_t* mc_m, int64_t cap_mc,
+                                int64_t* n_out) {
+    otrace tr;
+    memset(&tr, 0, sizeof(tr));
+    tr.cap_tri = cap_tri; tr.tri = tri;
+    tr.cap_mc = cap_mc; tr.mc_tri = mc_tri; tr.mc_pt = mc_pt;
+    tr.mc_mean = mc_mean; tr.mc_sig = mc_sig; tr.mc_m = mc_m;
+    int rc = tree_potential(X, N, eps, tau, alpha, leaf_size, m_limit, zeta, seed, mc_rule,
+                            seed_up, out, NULL, stats, &tr);
+    n_out[0] = tr.n_tri;
+    n_out[1] = tr.n_mc;
+    return rc;
+}
+
+/* The Monte Carlo partner draw alone (for tests): node triple P (node ids,
+ * equal ids = the same node) with point ranges [begin[s], end[s]) per slot,
+ * point x of slot `slot`; draw n partner pairs from the 32-bit words
+ * r[2m], r[2m+1] into yz[2m], yz[2m+1]. */
+int oracle_mc_draw(const int64_t P[3], const int64_t begin[3], const int64_t end[3], int slot,
+                   int64_t x, const uint32_t* r, int64_t n, int64_t* yz) {
+    int64_t b[3], e[3], Q[3];
+    Q[0] = 0;
+    Q[1] = P[1] == P[0] ? 0 : 1;
+    Q[2] = P[2] == P[1] ? Q[1] : 2;
+    for (int s = 0; s < 3; ++s) {
+        b[Q[s]] = begin[s];
+        e[Q[s]] = end[s];
+    }
+    otree t;
+    memset(&t, 0, sizeof(t));
+    t.begin = b;
+    t.end = e;
+    osolve S;
+    memset(&S, 0, sizeof(S));
+    S.t = &t;
+    for (int64_t m = 0; m < n; ++m)
+        draw_partners(&S, Q, slot, x, r[2 * m], r[2 * m + 1], yz + 2 * m, yz + 2 * m + 1);
     return 0;
 }
 

@@ -169,3 +169,28 @@ def test_hybrid_rule(gmm):
     assert np.all(np.abs(phi - ex) <= eps * np.abs(ex) + tau + FP32_BAR * ab)
     ref, _, rst = otree.tree_potential(X, eps=eps, tau=tau, alpha=0.0, with_counts=True)
     assert st["det_prunes"] == rst["det_prunes"]
+
+
+@pytest.mark.parametrize("case", ["tau", "tau_large", "monte_carlo"])
+def test_credits_on_pinned_set(case):
+    """The set on which the oracle's credited values are pinned (4-component
+    mixture, N = 400, leaf size 8): with a large tau, prunes of internal nodes
+    carry up to half of sum|phi| for some particles, so a slip in the GPU's
+    credit, centre of mass or top-down push shows far above the FP32 bar."""
+    X = np.ascontiguousarray(inputs.gaussian_mixture(400, 4, 7.0, 0.5, 1.5, 0.05, 5))
+    ex, ab = oracle.phi(X, with_abs=True)
+    med = float(np.median(np.abs(ex)))
+    if case == "monte_carlo":
+        phi, cnt, st = _gpu_tree(X, 0.1, 0.05, leaf_size=8, zeta=4.0)
+        ref, _, rst = otree.tree_potential(X, eps=0.1, alpha=0.05, zeta=4.0, leaf_size=8,
+                                           with_counts=True)
+        assert st["mc_prunes"] > 0
+        assert abs(st["mc_prunes"] - rst["mc_prunes"]) <= max(2, 0.02 * rst["mc_prunes"])
+        assert (np.abs(phi - ref) <= FP32_BAR * ab).mean() >= 0.99
+    else:
+        tau = 1e-3 * med if case == "tau" else 1e3 * med
+        phi, cnt, st = _gpu_tree(X, tau, 0.0, mode="tree_abs", leaf_size=8)
+        ref, _, rst = otree.tree_potential(X, eps=0.0, tau=tau, leaf_size=8, with_counts=True)
+        assert st["det_prunes"] == rst["det_prunes"] > 0
+        assert np.all(np.abs(phi - ref) <= FP32_BAR * ab)
+    assert np.all(cnt == comb(len(X) - 1, 2))

@@ -134,13 +134,10 @@ def test_mc_is_deterministic_in_seed(gmm):
 # oracle with one plausible slip (a Fig. 4 count, the budget's T^root),
 # compiled on its own; the pins (exact at eps = 0, tuple counts = C(N-1, 2),
 # the deterministic, absolute and Monte Carlo guarantees) must reject every
-# one of them and accept the unmodified copy. The value a prune credits is
-# not among them: with T^root in the budget every pruned contribution on
-# these sets is far below the allowed error (a copy that drops them all, or
-# credits them all to the first node, still meets eps and tau), so that part
-# is checked by the agreement of the two independent implementations (GPU vs
-# oracle to 3e-6 sum|phi| per particle, while such a slip moves Phi by
-# ~1e-4 |Phi|).
+# one of them and accept the unmodified copy. Slips in the values a prune
+# credits, in the Monte Carlo sampler and in the top-down push pass these
+# pins (with T^root in the budget a pruned contribution is far below the
+# allowed error); test_tree_oracle_credit.py pins those steps.
 # ---------------------------------------------------------------------------
 _TREE_MUTANTS = {
     "control": None,
