@@ -266,6 +266,9 @@ typedef struct {
     double compute_ms;     /* start -> result in out_host */
     double latency_ms;     /* submit -> result in out_host */
     int64_t bytes_reserved;/* footprint estimate admitted against the budget */
+    int64_t dev_start_ns;  /* device clock (%globaltimer, ns) when the solve's first kernel */
+    int64_t dev_end_ns;    /* started / after its last kernel; intervals of requests that
+                              ran at once overlap (0 if the request failed) */
 } mbm_result;
 
 /* Create a server on `device` with `slots` (1..64) workers and an HBM budget

@@ -63,7 +63,8 @@ class Request(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32),
                 ("queue_ms", ctypes.c_double), ("compute_ms", ctypes.c_double),
-                ("latency_ms", ctypes.c_double), ("bytes_reserved", ctypes.c_int64)]
+                ("latency_ms", ctypes.c_double), ("bytes_reserved", ctypes.c_int64),
+                ("dev_start_ns", ctypes.c_int64), ("dev_end_ns", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

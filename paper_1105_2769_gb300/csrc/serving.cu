@@ -10,6 +10,14 @@
 // requests for the same id skip the copy and the build. Admission is FIFO
 // with backfill: the oldest request has priority, and a younger one may start
 // only if it fits beside the room held for the oldest.
+//
+// A resident system is published only with a CUDA event recorded after its
+// upload and tree build on the creating slot's stream; every other slot
+// makes its stream wait on that event before reading the system, so no slot
+// reads points or a tree that are still being written. Evicted systems are
+// taken off the table under the server lock and freed after it is released
+// (freeing waits for the device), so submit, poll and the other slots never
+// wait on device work through the lock.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -49,6 +57,7 @@ struct Resident {
     int64_t N = 0;
     double* X = nullptr;
     mbm_tree* tree = nullptr;
+    cudaEvent_t ready = nullptr;  // recorded after the upload and the tree build
     size_t bytes = 0;
     int users = 0;
     uint64_t last_use = 0;
@@ -61,6 +70,8 @@ struct Worker {
     double* dX = nullptr;  // private input/output buffers (grown on demand)
     double* dOut = nullptr;
     size_t capX = 0, capOut = 0;
+    unsigned long long* d_stamp = nullptr;  // device clock at a request's start and end
+    unsigned long long* h_stamp = nullptr;  // pinned host copy
 };
 
 size_t estimate_bytes(const mbm_request& r, const mbm_config& c) {
@@ -81,6 +92,7 @@ struct mbm_server {
     std::deque<Job> pending;
     std::unordered_map<uint64_t, Done> done;
     std::unordered_map<uint64_t, Resident> resident;
+    std::vector<Resident> evicted;  // off the table, not yet freed
     uint64_t next_ticket = 1, use_clock = 0;
     int64_t n_admitted = 0, n_rejected = 0, n_completed = 0;
     bool stop = false;
@@ -90,7 +102,16 @@ struct mbm_server {
 
 namespace {
 
-// Free resident systems nobody uses until `need` more bytes fit (LRU).
+void free_resident(Resident& r) {
+    if (r.tree) mbm_tree_free(r.tree);
+    if (r.X) cudaFree(r.X);
+    if (r.ready) cudaEventDestroy(r.ready);
+    r = Resident{};
+}
+
+// Take resident systems nobody uses off the table until `need` more bytes
+// fit (LRU); the caller holds the lock, and they are freed after it is
+// released (s->evicted).
 void evict_for(mbm_server* s, size_t need) {
     while (s->budget && s->reserved + need > s->budget) {
         auto victim = s->resident.end();
@@ -99,9 +120,8 @@ void evict_for(mbm_server* s, size_t need) {
                 (victim == s->resident.end() || it->second.last_use < victim->second.last_use))
                 victim = it;
         if (victim == s->resident.end()) return;
-        if (victim->second.tree) mbm_tree_free(victim->second.tree);
-        if (victim->second.X) cudaFree(victim->second.X);
         s->reserved -= victim->second.bytes;
+        s->evicted.push_back(victim->second);
         s->resident.erase(victim);
     }
 }
@@ -138,13 +158,37 @@ mbm_status grow(double** p, size_t* cap, size_t bytes) {
     return MBM_OK;
 }
 
+// Device clock (%globaltimer, ns) at this point of the stream's work.
+__global__ void stamp_kernel(unsigned long long* t) {
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    *t = v;
+}
+
+// Solve one request on this worker's stream with inputs X (and tree) in place.
+mbm_status solve_job(Worker& w, const Job& job, const double* X, mbm_tree* tree, size_t ob) {
+    const mbm_request& r = job.req;
+    MBM_TRY(grow(&w.dOut, &w.capOut, ob));
+    mbm_stream_t ms = reinterpret_cast<mbm_stream_t>(w.stream);
+    stamp_kernel<<<1, 1, 0, w.stream>>>(w.d_stamp);
+    mbm_status st;
+    if (r.kind == MBM_REQ_FORCES) st = mbm_forces(w.ctx, X, r.N, r.eps, r.alpha, r.mode, w.dOut, ms);
+    else st = mbm_potential_ex(w.ctx, X, r.N, r.eps, r.alpha, r.mode, &job.cfg, tree, w.dOut, nullptr, ms);
+    stamp_kernel<<<1, 1, 0, w.stream>>>(w.d_stamp + 1);
+    if (st != MBM_OK) return st;
+    MBM_CUDA_TRY(cudaMemcpyAsync(w.h_stamp, w.d_stamp, 2 * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, w.stream));
+    MBM_CUDA_TRY(cudaMemcpyAsync(r.out_host, w.dOut, ob, cudaMemcpyDeviceToHost, w.stream));
+    return MBM_OK;
+}
+
 mbm_status run_job(mbm_server* s, Worker& w, const Job& job, int slot, mbm_result& res) {
     const mbm_request& r = job.req;
     const size_t xb = (size_t)r.N * 24;
     const size_t ob = (size_t)r.N * (r.kind == MBM_REQ_FORCES ? 24 : 8);
     const bool tree_mode = (r.mode & 0xff) == MBM_TREE;
-    double* X = nullptr;
-    mbm_tree* tree = nullptr;
+    res.slot = slot;
+    w.h_stamp[0] = w.h_stamp[1] = 0;
     Resident* res_entry = nullptr;
     if (r.system_id) {
         std::unique_lock<std::mutex> lock(s->mu);
@@ -155,66 +199,78 @@ mbm_status run_job(mbm_server* s, Worker& w, const Job& job, int slot, mbm_resul
             res_entry->last_use = ++s->use_clock;
         }
     }
+    mbm_status st = MBM_OK;
     if (res_entry) {
-        X = res_entry->X;
-        tree = res_entry->tree;
+        // the creator's upload and build may still be running on its stream
+        cudaError_t e = cudaStreamWaitEvent(w.stream, res_entry->ready, 0);
+        st = e == cudaSuccess ? solve_job(w, job, res_entry->X, res_entry->tree, ob)
+                              : mbm_cuda_fail(e, "cudaStreamWaitEvent(resident system)");
     } else if (r.system_id) {
         // first request for this system: make it resident
         double* dx = nullptr;
-        MBM_CUDA_TRY(cudaMalloc(&dx, xb));
-        MBM_CUDA_TRY(cudaMemcpyAsync(dx, r.X_host, xb, cudaMemcpyHostToDevice, w.stream));
         mbm_tree* t = nullptr;
-        if (tree_mode && r.N >= 3) {
-            mbm_status st = mbm_tree_build(w.ctx, dx, r.N, &job.cfg, w.stream, &t);
-            if (st != MBM_OK) {
-                cudaFree(dx);
-                return st;
+        cudaEvent_t ready = nullptr;
+        cudaError_t e = cudaMalloc(&dx, xb);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dx, r.X_host, xb, cudaMemcpyHostToDevice, w.stream);
+        if (e != cudaSuccess) st = mbm_cuda_fail(e, "upload of a resident system");
+        if (st == MBM_OK && tree_mode && r.N >= 3)
+            st = mbm_tree_build(w.ctx, dx, r.N, &job.cfg, w.stream, &t);
+        if (st == MBM_OK) {
+            e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(ready, w.stream);
+            if (e != cudaSuccess) st = mbm_cuda_fail(e, "cudaEventRecord(resident system)");
+        }
+        if (st != MBM_OK) {
+            cudaStreamSynchronize(w.stream);
+            if (ready) cudaEventDestroy(ready);
+            if (t) mbm_tree_free(t);
+            if (dx) cudaFree(dx);
+            return st;
+        }
+        bool shared = false;
+        {
+            std::unique_lock<std::mutex> lock(s->mu);
+            Resident ent;
+            ent.N = r.N;
+            ent.X = dx;
+            ent.tree = t;
+            ent.ready = ready;
+            ent.bytes = xb + (t ? (size_t)r.N * 72 : 0);
+            ent.users = 1;
+            ent.last_use = ++s->use_clock;
+            auto ins = s->resident.emplace(r.system_id, ent);
+            if (ins.second) {
+                s->reserved += ent.bytes;
+                res_entry = &ins.first->second;
+                shared = true;
             }
         }
-        std::unique_lock<std::mutex> lock(s->mu);
-        Resident e;
-        e.N = r.N;
-        e.X = dx;
-        e.tree = t;
-        e.bytes = xb + (t ? (size_t)r.N * 72 : 0);
-        e.users = 1;
-        e.last_use = ++s->use_clock;
-        s->reserved += e.bytes;
-        auto ins = s->resident.emplace(r.system_id, e);
-        if (!ins.second) {  // another slot made it resident meanwhile: use ours privately
-            s->reserved -= e.bytes;
-            lock.unlock();
-            X = dx;
-            tree = t;
-        } else {
-            res_entry = &ins.first->second;
-            X = dx;
-            tree = t;
+        st = solve_job(w, job, dx, t, ob);
+        if (!shared) {  // another slot made it resident meanwhile: ours stays private
+            cudaStreamSynchronize(w.stream);
+            cudaEventDestroy(ready);
+            if (t) mbm_tree_free(t);
+            cudaFree(dx);
         }
     } else {
-        MBM_TRY(grow(&w.dX, &w.capX, xb));
-        MBM_CUDA_TRY(cudaMemcpyAsync(w.dX, r.X_host, xb, cudaMemcpyHostToDevice, w.stream));
-        X = w.dX;
-    }
-    MBM_TRY(grow(&w.dOut, &w.capOut, ob));
-    mbm_status st;
-    mbm_stream_t ms = reinterpret_cast<mbm_stream_t>(w.stream);
-    if (r.kind == MBM_REQ_FORCES) st = mbm_forces(w.ctx, X, r.N, r.eps, r.alpha, r.mode, w.dOut, ms);
-    else st = mbm_potential_ex(w.ctx, X, r.N, r.eps, r.alpha, r.mode, &job.cfg, tree, w.dOut, nullptr, ms);
-    if (st == MBM_OK) {
-        cudaError_t e = cudaMemcpyAsync(r.out_host, w.dOut, ob, cudaMemcpyDeviceToHost, w.stream);
-        if (e != cudaSuccess) st = mbm_cuda_fail(e, "cudaMemcpyAsync(result)");
+        st = grow(&w.dX, &w.capX, xb);
+        if (st == MBM_OK) {
+            cudaError_t e = cudaMemcpyAsync(w.dX, r.X_host, xb, cudaMemcpyHostToDevice, w.stream);
+            st = e == cudaSuccess ? solve_job(w, job, w.dX, nullptr, ob)
+                                  : mbm_cuda_fail(e, "upload of a request");
+        }
     }
     cudaError_t e = cudaStreamSynchronize(w.stream);
     if (e != cudaSuccess && st == MBM_OK) st = mbm_cuda_fail(e, "cudaStreamSynchronize");
     if (res_entry) {
         std::unique_lock<std::mutex> lock(s->mu);
         res_entry->users--;
-    } else if (r.system_id) {  // private copy of a system that another slot made resident
-        if (tree) mbm_tree_free(tree);
-        cudaFree(X);
     }
-    res.slot = slot;
+    if (st == MBM_OK) {
+        res.dev_start_ns = (int64_t)w.h_stamp[0];
+        res.dev_end_ns = (int64_t)w.h_stamp[1];
+    }
     return st;
 }
 
@@ -223,11 +279,18 @@ void worker_main(mbm_server* s, int slot) {
     cudaSetDevice(s->device);
     for (;;) {
         Job job;
+        std::vector<Resident> dead;
         {
             std::unique_lock<std::mutex> lock(s->mu);
-            s->cv_work.wait(lock, [&] { return s->stop || take_job(s, job); });
-            if (s->stop && job.ticket == 0) return;
-            s->n_admitted++;
+            s->cv_work.wait(lock,
+                            [&] { return s->stop || !s->evicted.empty() || take_job(s, job); });
+            dead.swap(s->evicted);
+            if (job.ticket != 0) s->n_admitted++;
+        }
+        for (auto& d : dead) free_resident(d);  // outside the lock
+        if (job.ticket == 0) {
+            if (s->stop) return;
+            continue;
         }
         const clk::time_point t0 = clk::now();
         mbm_result res{};
@@ -263,14 +326,21 @@ extern "C" mbm_status mbm_server_create(int device, size_t hbm_budget_bytes, int
     s->budget = hbm_budget_bytes;
     s->workers.resize(slots);
     for (int i = 0; i < slots; ++i) {
-        mbm_status st = mbm_ctx_create(device, 0, &s->workers[i].ctx);
-        cudaError_t e = st == MBM_OK ? cudaStreamCreateWithFlags(&s->workers[i].stream,
-                                                                 cudaStreamNonBlocking)
+        Worker& w = s->workers[i];
+        mbm_status st = mbm_ctx_create(device, 0, &w.ctx);
+        cudaError_t e = st == MBM_OK ? cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking)
                                      : cudaSuccess;
+        if (st == MBM_OK && e == cudaSuccess)
+            e = cudaMalloc(&w.d_stamp, 2 * sizeof(unsigned long long));
+        if (st == MBM_OK && e == cudaSuccess)
+            e = cudaMallocHost(&w.h_stamp, 2 * sizeof(unsigned long long));
         if (st != MBM_OK || e != cudaSuccess) {
             for (int j = 0; j <= i; ++j) {
-                if (s->workers[j].stream) cudaStreamDestroy(s->workers[j].stream);
-                if (s->workers[j].ctx) mbm_ctx_destroy(s->workers[j].ctx);
+                Worker& v = s->workers[j];
+                if (v.d_stamp) cudaFree(v.d_stamp);
+                if (v.h_stamp) cudaFreeHost(v.h_stamp);
+                if (v.stream) cudaStreamDestroy(v.stream);
+                if (v.ctx) mbm_ctx_destroy(v.ctx);
             }
             delete s;
             return st != MBM_OK ? st : mbm_cuda_fail(e, "cudaStreamCreate");
@@ -292,13 +362,13 @@ extern "C" mbm_status mbm_server_destroy(mbm_server* s) {
     for (auto& w : s->workers)
         if (w.th.joinable()) w.th.join();
     cudaSetDevice(s->device);
-    for (auto& kv : s->resident) {
-        if (kv.second.tree) mbm_tree_free(kv.second.tree);
-        if (kv.second.X) cudaFree(kv.second.X);
-    }
+    for (auto& kv : s->resident) free_resident(kv.second);
+    for (auto& d : s->evicted) free_resident(d);
     for (auto& w : s->workers) {
         if (w.dX) cudaFree(w.dX);
         if (w.dOut) cudaFree(w.dOut);
+        if (w.d_stamp) cudaFree(w.d_stamp);
+        if (w.h_stamp) cudaFreeHost(w.h_stamp);
         if (w.stream) cudaStreamDestroy(w.stream);
         if (w.ctx) mbm_ctx_destroy(w.ctx);
     }

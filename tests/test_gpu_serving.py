@@ -97,3 +97,42 @@ def test_poll_pending_and_resident_system():
     b = srv.poll(srv.submit(X, mode="tree", eps=1e-2, alpha=0.0, system_id=42))[2]
     assert np.all(np.abs(a - b) <= 1e-10 * np.abs(a).max())
     srv.close()
+
+
+def test_concurrent_first_requests_for_one_system():
+    """Several requests for the same new system arrive at once on four slots:
+    whichever slot publishes the resident copy, the others either wait for its
+    upload and tree build (event) or solve privately; every result equals the
+    request solved alone."""
+    X = inputs.gaussian_mixture(3000, 4, 8.0, 0.5, 1.5, 0.05, 77)
+    ref = _alone(X, "potential", "tree", 1e-2, 0.05)
+    srv = api.Server(0, hbm_budget_bytes=4 << 30, slots=4)
+    for rep in range(3):
+        sid = 900 + rep
+        tickets = [srv.submit(X, mode="tree", eps=1e-2, alpha=0.05, system_id=sid)
+                   for _ in range(6)]
+        for t in tickets:
+            st, res, out = srv.poll(t)
+            assert st == 0
+            assert np.all(np.abs(out - ref) <= 1e-10 * np.abs(ref).max())
+    srv.close()
+
+
+def test_admitted_requests_overlap_on_the_device():
+    """Requests admitted together run at once: their device-clock intervals
+    (first kernel start to last kernel end, %globaltimer) overlap."""
+    srv = api.Server(0, hbm_budget_bytes=8 << 30, slots=4)
+    Xs = [inputs.uniform_cube(4096, 16.0, 0.5, 300 + q) for q in range(4)]
+    tickets = [srv.submit(X, kind="forces", mode="fp32") for X in Xs]
+    iv = []
+    for t in tickets:
+        st, res, _ = srv.poll(t)
+        assert st == 0 and res["dev_end_ns"] > res["dev_start_ns"] > 0
+        iv.append((res["dev_start_ns"], res["dev_end_ns"], res["slot"]))
+    srv.close()
+    iv.sort()
+    overlaps = sum(1 for a, b in zip(iv, iv[1:]) if b[0] < a[1])
+    print("device intervals (ms from first start):",
+          [((s - iv[0][0]) / 1e6, (e - iv[0][0]) / 1e6, sl) for s, e, sl in iv])
+    assert overlaps >= 1
+    assert len({sl for _, _, sl in iv}) >= 2
