@@ -194,7 +194,7 @@ def bench_fp64(api, inputs, torch, dev):
 
 
 def bench_tree(api, inputs, torch, dev, r64, np, workload="gmm4_n65536", eps_list=(1e-2, 1e-1),
-               warm=True, n_sample=32, progress=False):
+               warm=True, n_sample=256, progress=False):
     """Tree solves (relative eps, alpha 0.05) timed end to end from device-resident X;
     accuracy on n_sample seeded particles against the exact sampled sum."""
     X = inputs.workload(workload)

@@ -71,7 +71,13 @@ typedef struct {
     int32_t reserved0;
     int64_t* tuple_counts; /* optional device int64[N]: point triples credited to each
                               particle by prunes and base cases (validation; NULL = off) */
-    int32_t reserved[4];
+    /* Traversal buffer sizes, 0 = sized from N (the default). Smaller values
+     * change only how the work is batched, never a decision or a result:
+     * they exist so that small test problems run the paths large ones take. */
+    int32_t trav_chunk;    /* node triples classified per launch (>= 1) */
+    int32_t base_cap;      /* leaf triples per base-case flush (raised to >= trav_chunk) */
+    int32_t est_cap;       /* Monte Carlo estimates per batch (raised to >= N + 128) */
+    int32_t reserved1;
 } mbm_config;
 
 /* Counters of the last solve (tree path); all zero for exhaustive modes. */
@@ -85,6 +91,9 @@ typedef struct {
     int64_t mc_samples;     /* phi evaluations drawn by Monte Carlo */
     int64_t levels;         /* traversal levels */
     double ms_build, ms_seed, ms_traverse, ms_base, ms_finalize;
+    int64_t chunks;         /* classify launches */
+    int64_t base_flushes;   /* base-case flushes */
+    int64_t mc_batches;     /* Monte Carlo estimate batches */
 } mbm_stats;
 
 typedef struct mbm_ctx mbm_ctx;

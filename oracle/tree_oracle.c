@@ -557,22 +557,24 @@ static void recurse(osolve* S, int64_t P1, int64_t P2, int64_t P3) {
     }
 }
 
-/* exact seed: for each point, sum over triples inside its seed node */
+int oracle_phi(const double* X, int64_t N, const int64_t* idx, int64_t n_idx, double* out,
+               double* absout, int nthreads);
+
+/* exact seed: for each point, the exact sum (Eq. 1) over the triples inside
+ * its seed node, i.e. Phi of the point within the seed node's point set */
 static void seed_phil(otree* t, int seed_up) {
     int64_t N = t->N;
     double* seed = (double*)calloc((size_t)N, sizeof(double));
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+    for (int64_t p = 0; p < N; ++p) idx[p] = p;
     int sd = t->depth - seed_up;
     if (sd < 0) sd = 0;
     int64_t first = ((int64_t)1 << sd) - 1;
     for (int64_t q = 0; q < ((int64_t)1 << sd); ++q) {
-        int64_t v = first + q;
-        for (int64_t i = t->begin[v]; i < t->end[v]; ++i)
-            for (int64_t j = i + 1; j < t->end[v]; ++j)
-                for (int64_t k = j + 1; k < t->end[v]; ++k) {
-                    double f = oracle_at_phi(t->Xs + 3 * i, t->Xs + 3 * j, t->Xs + 3 * k);
-                    seed[i] += f; seed[j] += f; seed[k] += f;
-                }
+        int64_t v = first + q, b = t->begin[v], n = t->end[v] - t->begin[v];
+        oracle_phi(t->Xs + 3 * b, n, idx, n, seed + b, NULL, 0);
     }
+    free(idx);
     t->pphil = (double*)malloc(sizeof(double) * (size_t)N);
     for (int64_t p = 0; p < N; ++p) t->pphil[p] = fabs(seed[p]);
     for (int64_t v = 0; v < t->n_nodes; ++v) {

@@ -32,7 +32,8 @@ class Config(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("mc_rule", ctypes.c_int32),
                 ("validate", ctypes.c_int32), ("seed_levels", ctypes.c_int32),
                 ("reserved0", ctypes.c_int32), ("tuple_counts", ctypes.c_void_p),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("trav_chunk", ctypes.c_int32), ("base_cap", ctypes.c_int32),
+                ("est_cap", ctypes.c_int32), ("reserved1", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -42,7 +43,8 @@ class Stats(ctypes.Structure):
                 ("mc_samples", ctypes.c_int64), ("levels", ctypes.c_int64),
                 ("ms_build", ctypes.c_double), ("ms_seed", ctypes.c_double),
                 ("ms_traverse", ctypes.c_double), ("ms_base", ctypes.c_double),
-                ("ms_finalize", ctypes.c_double)]
+                ("ms_finalize", ctypes.c_double), ("chunks", ctypes.c_int64),
+                ("base_flushes", ctypes.c_int64), ("mc_batches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -1319,12 +1319,15 @@ struct TravPlan {
     std::vector<size_t> parts;
 };
 
-TravPlan trav_plan(int64_t N, int depth, int m_limit, bool counting) {
+TravPlan trav_plan(int64_t N, int depth, const mbm_config& cfg) {
+    const int m_limit = cfg.m_limit;
+    const bool counting = cfg.tuple_counts != nullptr;
     TravPlan q;
     const int64_t n_nodes = ((int64_t)2 << depth) - 1, n_leaves = (int64_t)1 << depth;
     // Frontier chunk B: a chunk of B node triples yields at most 4B children,
     // B Monte Carlo candidates and B base cases, so no list can overflow.
     q.B = std::max<int64_t>(1 << 14, std::min<int64_t>(1 << 20, 16 * N));
+    if (cfg.trav_chunk > 0) q.B = cfg.trav_chunk;
     q.max_levels = 3 * depth + 8;
     q.cap_lvl = 4 * q.B;
     q.cap_mc = q.B;
@@ -1335,8 +1338,12 @@ TravPlan trav_plan(int64_t N, int depth, int m_limit, bool counting) {
     const double all = L * (L + 1.0) * (L + 2.0) / 6.0;
     int64_t want = std::min<int64_t>(1 << 27, std::max<int64_t>(1 << 22, 512 * N));
     if ((double)want > all) want = (int64_t)all;
+    if (cfg.base_cap > 0) want = cfg.base_cap;
     q.cap_base = std::max<int64_t>(q.B, want);
+    // one candidate's estimates (its distinct nodes are disjoint, rounded up
+    // to 32-point chunks) never exceed N + 96, so every batch holds at least one
     q.cap_est = 3 * N + 64 * 1024;
+    if (cfg.est_cap > 0) q.cap_est = std::max<int64_t>(N + 128, cfg.est_cap);
     cub::DeviceScan::ExclusiveSum(nullptr, q.cub_bytes, (int64_t*)nullptr, (int64_t*)nullptr,
                                   (int)(q.cap_mc + 1));
     // Base-case grouping: radix sort of (y, z) keys over 2 * depth bits and a
@@ -1604,7 +1611,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
 
     const int64_t n_nodes = tree->n_nodes, n_leaves = tree->n_leaves;
     const bool counting = cfg.tuple_counts != nullptr;
-    const TravPlan plan = trav_plan(N, tree->depth, cfg.m_limit, counting);
+    const TravPlan plan = trav_plan(N, tree->depth, cfg);
     const int64_t B = plan.B, cap_lvl = plan.cap_lvl, cap_mc = plan.cap_mc;
     const int64_t cap_base = plan.cap_base, cap_est = plan.cap_est;
     const int max_levels = plan.max_levels;
@@ -1745,7 +1752,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         int64_t count, done;
     };
     std::vector<Level> stack{{1, 0}};
-    int64_t n_base = 0, levels_seen = 1;
+    int64_t n_base = 0, levels_seen = 1, n_chunks = 0, n_flushes = 0, n_batches = 0;
     std::vector<int64_t> off;
     while (!stack.empty()) {
         const int li = (int)stack.size() - 1;
@@ -1757,6 +1764,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         const int64_t take = std::min<int64_t>(B, stack[li].count - stack[li].done);
         if (n_base + take > cap_base) {
             MBM_TRY(flush_base(n_base));
+            n_flushes += n_base > 0;
             n_base = 0;
             MBM_CUDA_TRY(cudaMemsetAsync(ctr + 2, 0, sizeof(ull), s));
         }
@@ -1765,6 +1773,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         MBM_CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(ull), s));  // n_next, n_mc
         classify_kernel<<<grid_of(take, 256), 256, 0, s>>>(cur, take, p);
         MBM_CUDA_TRY(cudaGetLastError());
+        ++n_chunks;
         stack[li].done += take;
         MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 3 * sizeof(ull), cudaMemcpyDeviceToHost, s));
         MBM_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1791,6 +1800,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
                 mc_commit_kernel<<<(unsigned)(c1 - c0), 256, 0, s>>>(
                     mcl + c0, 0, c1 - c0, chunk_off + c0, cand_fail + c0, est, p);
                 MBM_CUDA_TRY(cudaGetLastError());
+                ++n_batches;
                 c0 = c1;
             }
             MBM_CUDA_TRY(cudaMemcpyAsync(h, ctr, 3 * sizeof(ull), cudaMemcpyDeviceToHost, s));
@@ -1803,6 +1813,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         }
     }
     MBM_TRY(flush_base(n_base));
+    n_flushes += n_base > 0;
     tm.mark(3);
     tm.mark(4);
     finalize_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, tree->depth, n_nodes, n_leaves, tree->perm,
@@ -1838,6 +1849,9 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         stats->ms_base = base_ms;
         stats->ms_finalize = tm.ms(4, 5);
         stats->base_triples = (int64_t)h[12];
+        stats->chunks = n_chunks;
+        stats->base_flushes = n_flushes;
+        stats->mc_batches = n_batches;
     }
     if (cfg.validate) return mbm_check_flags(ctx, s);
     return MBM_OK;
@@ -1847,6 +1861,6 @@ size_t mbm_tree_solve_bytes(int64_t N, const mbm_config& cfg) {
     if (N < 3 || cfg.leaf_size < 2) return 0;
     const int depth = tree_depth(N, cfg.leaf_size);
     const int64_t n_nodes = ((int64_t)2 << depth) - 1;
-    const TravPlan plan = trav_plan(N, depth, cfg.m_limit, cfg.tuple_counts != nullptr);
+    const TravPlan plan = trav_plan(N, depth, cfg);
     return carve_size(tree_parts(N, n_nodes)) + carve_size(plan.parts);
 }

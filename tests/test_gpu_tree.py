@@ -194,3 +194,61 @@ def test_credits_on_pinned_set(case):
         assert st["det_prunes"] == rst["det_prunes"] > 0
         assert np.all(np.abs(phi - ref) <= FP32_BAR * ab)
     assert np.all(cnt == comb(len(X) - 1, 2))
+
+
+@pytest.mark.parametrize("eps,alpha", [(0.01, 0.0), (0.1, 0.05)])
+def test_small_buffers_take_the_large_problem_paths(gmm, eps, alpha):
+    """Traversal chunks of 64 node triples, base-case flushes of at most 256
+    leaf triples and Monte Carlo batches of N + 128 estimates: the chunked
+    traversal, the mid-traversal base-case flushes and the batched Monte Carlo
+    estimates that large problems take all run many times, with the same
+    decisions and results as the serial restatement."""
+    X, ex, ab = gmm
+    small = dict(trav_chunk=64, base_cap=256, est_cap=1)
+    zeta = 4.0
+    phi, cnt, st = _gpu_tree(X, eps, alpha, zeta=zeta, **small)
+    ref, _, rst = otree.tree_potential(X, eps=eps, alpha=alpha, zeta=zeta, with_counts=True)
+    print(f"eps={eps} alpha={alpha}: chunks {st['chunks']}, base flushes {st['base_flushes']}, "
+          f"MC batches {st['mc_batches']}; det {st['det_prunes']}/{rst['det_prunes']}, "
+          f"mc {st['mc_prunes']}/{rst['mc_prunes']}")
+    assert st["chunks"] >= 50 and st["base_flushes"] >= 10
+    assert np.all(cnt == comb(len(X) - 1, 2))
+    assert st["det_prunes"] == rst["det_prunes"]
+    if alpha == 0.0:
+        assert st["node_triples_visited"] == rst["visited"]
+        assert np.all(np.abs(phi - ref) <= FP32_BAR * ab)
+    else:
+        assert st["mc_batches"] >= 2
+        assert abs(st["mc_prunes"] - rst["mc_prunes"]) <= max(2, 0.02 * rst["mc_prunes"])
+        assert (np.abs(phi - ref) <= FP32_BAR * ab).mean() >= 0.99
+    # and the default buffer sizes give the same result
+    phi_d, _, st_d = _gpu_tree(X, eps, alpha, zeta=zeta)
+    assert st_d["chunks"] < st["chunks"]
+    assert st_d["det_prunes"] == st["det_prunes"] and st_d["mc_prunes"] == st["mc_prunes"]
+    assert np.all(np.abs(phi_d - phi) <= 1e-9 * ab)
+
+
+@pytest.mark.parametrize("eps", [0.01, 0.1])
+def test_library_defaults_against_the_oracle(eps):
+    """The configuration the benchmark runs (seed node 6 levels above the
+    leaves, zeta = 32, m_limit = 256, leaf size 32) on a 2 048-point,
+    8-component mixture where Monte Carlo prunes at these defaults: the same
+    deterministic prunes as the restatement with the same settings, Monte
+    Carlo prune counts within 2 %, >= 99 % of particles equal to the FP32 bar,
+    and >= 1 - alpha within eps."""
+    X = np.ascontiguousarray(inputs.gaussian_mixture(2048, 8, 40.0, 0.5, 1.5, 0.05, 9))
+    ex, ab = oracle.phi(X, with_abs=True)
+    alpha = 0.05
+    d = _lib.default_config()
+    phi, cnt, st = _gpu_tree(X, eps, alpha, seed_levels=d.seed_levels)
+    ref, _, rst = otree.tree_potential(X, eps=eps, alpha=alpha, zeta=d.zeta, m_limit=d.m_limit,
+                                       seed_up=d.seed_levels, leaf_size=d.leaf_size,
+                                       with_counts=True)
+    print(f"eps={eps}: det {st['det_prunes']}/{rst['det_prunes']}, "
+          f"mc {st['mc_prunes']}/{rst['mc_prunes']}")
+    assert np.all(cnt == comb(len(X) - 1, 2))
+    assert st["mc_prunes"] > 0 and st["det_prunes"] == rst["det_prunes"]
+    assert abs(st["mc_prunes"] - rst["mc_prunes"]) <= max(2, 0.02 * rst["mc_prunes"])
+    assert (np.abs(phi - ref) <= FP32_BAR * ab).mean() >= 0.99
+    slack = 3.0 * np.sqrt(alpha * (1 - alpha) / len(X))
+    assert (np.abs(phi - ex) <= eps * np.abs(ex)).mean() >= 1 - alpha - slack
