@@ -183,9 +183,35 @@ void mbm_time_end(mbm_ctx* ctx, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Exhaustive solves (steps a1 + a2/a3).
 // ---------------------------------------------------------------------------
+// Largest N whose FP32-bulk solve reads a pair table (NT(NT+1)/2 blocks of
+// 16 KB: 8.6 GB at N = 32 768, 34 GB at 65 536). Larger sets, or a table that
+// does not fit the context's budget or the device, form pair terms in the
+// kernel instead (FP32 set-up, a few ulp per pair term).
+constexpr int64_t kPairTableMaxN = 65536;
+
 static mbm_status run_exhaustive(mbm_ctx* ctx, const double* X, int64_t N, int mode, double* phi,
                                  int validate, cudaStream_t s) {
     const size_t hdr = 256;  // work counter
+    if (mode == MBM_EXH_FP32 && N <= kPairTableMaxN) {
+        const size_t tb = pair_table_bytes(N);
+        const mbm_status rs = mbm_scratch_reserve(ctx, hdr + tb);
+        if (rs == MBM_OK) {
+            char* base = static_cast<char*>(ctx->scratch);
+            auto* counter = reinterpret_cast<unsigned long long*>(base);
+            MBM_CUDA_TRY(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+            MBM_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+            MBM_CUDA_TRY(cudaMemsetAsync(phi, 0, (size_t)N * sizeof(double), s));
+            MBM_CUDA_TRY(launch_pair_table(X, N, base + hdr, ctx->d_flags, s));
+            mbm_time_begin(ctx, s);
+            MBM_CUDA_TRY(launch_exh_fp32_table(base + hdr, N, phi, counter, ctx->d_flags,
+                                               ctx->num_sms, s));
+            mbm_time_end(ctx, s);
+            if (validate) return mbm_check_flags(ctx, s);
+            return MBM_OK;
+        }
+        if (rs != MBM_EBUDGET && rs != MBM_ENOMEM) return rs;
+        cudaGetLastError();  // clear a failed allocation; take the path without a table
+    }
     const size_t pack = mode == MBM_EXH_FP32 ? (size_t)N * 2 * sizeof(float4)
                                              : (size_t)N * sizeof(double4_32a);
     MBM_TRY(mbm_scratch_reserve(ctx, hdr + pack));

@@ -21,6 +21,9 @@
 // Diagonal tiles (I = J, J = K) are handled by zeroing the pair factor of
 // out-of-order pairs, so masked triples contribute exactly 0. Items come
 // from a global counter, largest (most I tiles) first.
+#include <algorithm>
+
+#include "bulk_copy.cuh"
 #include "device_math.cuh"
 #include "mbm_internal.h"
 #include "tile_fp32.cuh"
@@ -135,6 +138,165 @@ exh_fp32_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, in
             if (idx < N) atomicAdd(&phi[idx], tot);
         }
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step a3 with a pair table. Every pair term the FP32 sweep uses -- the unit
+// vector e_ab = (x_b - x_a)/r_ab and rho_ab = r_ab^-3 of each pair a < b -- is
+// computed once per solve in FP64 from the FP64 input and rounded once to
+// FP32, so each is correctly rounded (the in-kernel FP32 set-up carries a few
+// ulp), and the sweep no longer spends FP32 pipe time or MUFU work on pair
+// set-up. Layout: one 16 KB mbm_tile::PairBlock per tile pair (A, B),
+// A <= B, blocks of row A contiguous; a block holds the pair terms from
+// particle A*32 + r to B*32 + c in two planes indexed [c / 2][r]. Entries of
+// pairs that are absent (beyond N) or not ordered (A == B, r >= c) are zero.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ long long pt_block(int A, int B, int NT) {
+    return (long long)A * NT - (long long)A * (A - 1) / 2 + (B - A);
+}
+
+__global__ void __launch_bounds__(256)
+pair_table_kernel(const double* __restrict__ X, int N, int NT,
+                  mbm_tile::PairBlock* __restrict__ pt, int* __restrict__ flags) {
+    const int A = blockIdx.y;
+    const long long per_row = (long long)(NT - A) * (kTile * kTile / 2);
+    mbm_tile::PairBlock* rowbase = pt + pt_block(A, A, NT);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < per_row;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int B = A + (int)(q >> 9);
+        const int p = (int)(q >> 5) & 15, r = (int)q & 31;
+        const int a = A * kTile + r;
+        float v[2][4];
+        int bad = 0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int col = 2 * p + c, b = B * kTile + col;
+            v[c][0] = v[c][1] = v[c][2] = v[c][3] = 0.f;
+            if (a < N && b < N && (A < B || r < col)) {
+                const double dx = X[3 * (int64_t)b] - X[3 * (int64_t)a];
+                const double dy = X[3 * (int64_t)b + 1] - X[3 * (int64_t)a + 1];
+                const double dz = X[3 * (int64_t)b + 2] - X[3 * (int64_t)a + 2];
+                const double s2 = dx * dx + dy * dy + dz * dz;
+                if (!isfinite(s2)) {
+                    bad |= MBM_FLAG_NONFINITE;
+                } else if (!(s2 > 0.0)) {
+                    bad |= MBM_FLAG_COINCIDENT;
+                } else {
+                    const double y = 1.0 / sqrt(s2);
+                    v[c][0] = (float)(dx * y);
+                    v[c][1] = (float)(dy * y);
+                    v[c][2] = (float)(dz * y);
+                    v[c][3] = (float)(y * y * y);
+                }
+            }
+        }
+        if (bad) atomicOr(flags, bad);
+        mbm_tile::PairBlock& blk = rowbase[B - A];
+        blk.xy[p][r] = make_float4(v[0][0], v[1][0], v[0][1], v[1][1]);
+        blk.zr[p][r] = make_float4(v[0][2], v[1][2], v[0][3], v[1][3]);
+    }
+}
+
+struct PtSmem {
+    mbm_tile::PairBlock tab[2];  // (j, k) table of this item and the next
+    float redJ[kWarps32][kTile][kTile + 1];
+    float redK[kWarps32][kTile][kTile + 1];
+    double wsum[2][kWarps32][kTile];
+    unsigned long long bar[2];
+    long long item[2];
+};
+
+// An item's (j, k) table is block (J, K) of the pair table: one 16 KB bulk
+// copy, issued by thread 0 one item ahead.
+__device__ __forceinline__ void issue_item_table(PtSmem& sm, int buf, long long t, int NT,
+                                                 const mbm_tile::PairBlock* pt) {
+    int J, K;
+    decode_pair_item(t, NT, J, K);
+    const unsigned bytes = (unsigned)sizeof(mbm_tile::PairBlock);
+    mbar_arrive_expect_tx(&sm.bar[buf], bytes);
+    bulk_copy_g2s(&sm.tab[buf], pt + pt_block(J, K, NT), bytes, &sm.bar[buf]);
+}
+
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: a copy that never lands
+
+__global__ void __launch_bounds__(kWarps32 * 32, 2)
+exh_fp32_pt_kernel(const mbm_tile::PairBlock* __restrict__ pt, int N, int NT, long long n_items,
+                   unsigned long long* __restrict__ counter, double* __restrict__ phi,
+                   int* __restrict__ flags) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    PtSmem& sm = *reinterpret_cast<PtSmem*>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        mbar_fence_init();
+        const long long t = (long long)atomicAdd(counter, 1ULL);
+        sm.item[0] = t;
+        if (t < n_items) issue_item_table(sm, 0, t, NT, pt);
+    }
+    __syncthreads();
+    unsigned parity[2] = {0u, 0u};
+    bool pending[2] = {sm.item[0] < n_items, false};  // thread 0: copy issued, not yet waited
+    int buf = 0;
+    for (;;) {
+        const long long t = sm.item[buf];
+        if (t >= n_items) break;
+        if (threadIdx.x == 0) {
+            const long long tn = (long long)atomicAdd(counter, 1ULL);
+            sm.item[buf ^ 1] = tn;
+            if (tn < n_items) {
+                issue_item_table(sm, buf ^ 1, tn, NT, pt);
+                pending[buf ^ 1] = true;
+            }
+        }
+        const bool ok = mbar_wait_bounded(&sm.bar[buf], parity[buf], kWaitCycles);
+        if (ok) {
+            parity[buf] ^= 1u;
+            pending[buf] = false;
+        }
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicOr(flags, MBM_FLAG_TIMEOUT);
+            break;
+        }
+        int J, K;
+        decode_pair_item(t, NT, J, K);
+        double run_j = 0.0, run_k = 0.0;
+        for (int I = warp; I <= J; I += kWarps32) {
+            const int i = I * kTile + lane;
+            // the warp's next (I, K) block is streamed from memory: ask L2 for it now
+            if (I + kWarps32 <= J) {
+                const char* nb = reinterpret_cast<const char*>(pt + pt_block(I + kWarps32, K, NT));
+                for (int o = lane * 128; o < (int)sizeof(mbm_tile::PairBlock); o += 32 * 128)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(nb + o));
+            }
+            const float acc_i = mbm_tile::tile_triples_table(
+                sm.tab[buf], pt + pt_block(I, K, NT), pt + pt_block(I, J, NT), lane,
+                sm.redJ[warp], sm.redK[warp]);
+            run_j += (double)mbm_tile::row_sum(sm.redJ[warp], lane);
+            run_k += (double)mbm_tile::row_sum(sm.redK[warp], lane);
+            __syncwarp();
+            if (i < N) atomicAdd(&phi[i], (double)acc_i);
+        }
+        sm.wsum[0][warp][lane] = run_j;
+        sm.wsum[1][warp][lane] = run_k;
+        __syncthreads();
+        if (warp < 2) {
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarps32; ++w) tot += sm.wsum[warp][w][lane];
+            const int idx = (warp == 0 ? J : K) * kTile + lane;
+            if (idx < N) atomicAdd(&phi[idx], tot);
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+    // A copy is still in flight here only after a timed-out wait: give each
+    // one a bounded chance to land before the CTA's shared memory is released.
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b)
+            if (pending[b]) mbar_wait_bounded(&sm.bar[b], parity[b], kWaitCycles);
     }
 }
 
@@ -370,6 +532,36 @@ cudaError_t launch_exh_fp32(const float4* xhi, const float4* xlo, int64_t N, dou
     if (e != cudaSuccess) return e;
     const int grid = grid_for((const void*)exh_fp32_kernel, threads, smem, num_sms, items);
     exh_fp32_kernel<<<grid, threads, smem, s>>>(xhi, xlo, (int)N, NT, items, counter, phi, flags);
+    return cudaGetLastError();
+}
+
+size_t pair_table_bytes(int64_t N) {
+    const long long NT = (N + kTile - 1) / kTile;
+    return (size_t)(NT * (NT + 1) / 2) * sizeof(mbm_tile::PairBlock);
+}
+
+cudaError_t launch_pair_table(const double* X, int64_t N, void* table, int* flags, cudaStream_t s) {
+    const int NT = (int)((N + kTile - 1) / kTile);
+    const long long per_row0 = (long long)NT * (kTile * kTile / 2);
+    const int gx = (int)std::min<long long>((per_row0 + 255) / 256, 1024);
+    pair_table_kernel<<<dim3(gx, NT), 256, 0, s>>>(X, (int)N, NT,
+                                                   static_cast<mbm_tile::PairBlock*>(table), flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exh_fp32_table(const void* table, int64_t N, double* phi,
+                                  unsigned long long* counter, int* flags, int num_sms,
+                                  cudaStream_t s) {
+    const int NT = (int)((N + kTile - 1) / kTile);
+    const long long items = (long long)NT * (NT + 1) / 2;
+    const int threads = kWarps32 * 32;
+    const size_t smem = sizeof(PtSmem);
+    cudaError_t e = cudaFuncSetAttribute((const void*)exh_fp32_pt_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_for((const void*)exh_fp32_pt_kernel, threads, smem, num_sms, items);
+    exh_fp32_pt_kernel<<<grid, threads, smem, s>>>(
+        static_cast<const mbm_tile::PairBlock*>(table), (int)N, NT, items, counter, phi, flags);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,13 @@ cudaError_t launch_pack_f64(const double* X, int64_t N, double4_32a* x4, int* fl
 cudaError_t launch_exh_fp32(const float4* xhi, const float4* xlo, int64_t N, double* phi,
                             unsigned long long* counter, int* flags, int num_sms,
                             cudaStream_t s);
+// Pair table of the FP32-bulk sum (unit vector and r^-3 of every pair, FP64
+// rounded once to FP32): its size, its build from X, and the sum that reads it.
+size_t pair_table_bytes(int64_t N);
+cudaError_t launch_pair_table(const double* X, int64_t N, void* table, int* flags, cudaStream_t s);
+cudaError_t launch_exh_fp32_table(const void* table, int64_t N, double* phi,
+                                  unsigned long long* counter, int* flags, int num_sms,
+                                  cudaStream_t s);
 cudaError_t launch_exh_fp64(const double4_32a* x4, int64_t N, double* phi, unsigned long long* counter,
                             int* flags, int num_sms, cudaStream_t s);
 // Exact FP32-bulk Phi of sampled particles idx[0..n_idx) (out zeroed by the caller).

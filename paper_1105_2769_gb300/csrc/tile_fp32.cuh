@@ -90,6 +90,43 @@ __device__ __forceinline__ bool build_table_entry(TabPair (*tab)[kTile / 2], int
     return bad;
 }
 
+// One row j against the 8 column pairs (16 columns k) held in registers:
+// the 14-operation loop of the header comment. Column pair p of the row is
+// xy[p * stride], zr[p * stride] (float4: (ex_k, ex_k+1, ey_k, ey_k+1) and
+// (ez_k, ez_k+1, rho_k, rho_k+1)). Adds q rho_ij to the column accumulators
+// acc[p] and returns the packed row sum sum_k q rho_ik (the caller multiplies
+// by rho_ij).
+__device__ __forceinline__ float2 row_half(const float4* xy, const float4* zr, int stride,
+                                           const float2* vx, const float2* vy, const float2* vz,
+                                           const float2* rk, float2* acc, float2 ux, float2 uy,
+                                           float2 uz, float2 u3x, float2 u3y, float2 u3z,
+                                           float2 rij2) {
+    float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+        const float4 t0 = xy[p * stride];
+        const float4 t1 = zr[p * stride];
+        const float2 wx = make_float2(t0.x, t0.y);
+        const float2 wy = make_float2(t0.z, t0.w);
+        const float2 wz = make_float2(t1.x, t1.y);
+        const float2 rjk = make_float2(t1.z, t1.w);
+        float2 p1 = f2_mul(u3x, vx[p]);                // -3 cos t_i
+        p1 = f2_fma(u3y, vy[p], p1);
+        p1 = f2_fma(u3z, vz[p], p1);
+        float2 p2 = f2_mul(ux, wx);                    // -cos t_j
+        p2 = f2_fma(uy, wy, p2);
+        p2 = f2_fma(uz, wz, p2);
+        float2 p3 = f2_mul(vx[p], wx);                 // cos t_k
+        p3 = f2_fma(vy[p], wy, p3);
+        p3 = f2_fma(vz[p], wz, p3);
+        const float2 t = f2_mul(f2_mul(p1, p2), p3);   // 3 cos cos cos
+        const float2 q = f2_fma(t, rjk, rjk);          // (1 + 3 cos cos cos) rho_jk
+        s2 = f2_fma(q, rk[p], s2);                     // row sum (x rho_ij later)
+        acc[p] = f2_fma(q, rij2, acc[p]);              // column sums (x rho_ik later)
+    }
+    return s2;
+}
+
 // All triples of one I tile against the table (J rows x K columns).
 //   ih, il         : lane's particle (hi/lo); iv: lane holds a particle
 //   sJh/sJl, sKh/sKl: tile coordinates in shared memory
@@ -139,34 +176,78 @@ __device__ __forceinline__ float tile_triples(const TabPair (*tab)[kTile / 2], c
                          u3z = f2_splat(-3.0f * ez);
             const float rij = v ? pu.rho : 0.f;
             const float2 rij2 = f2_splat(rij);
-            float2 s2 = make_float2(0.f, 0.f);
             const TabPair* row = tab[jj] + (kb >> 1);
-#pragma unroll
-            for (int p = 0; p < kPairs; ++p) {
-                const float4 t0 = row[p].xy;
-                const float4 t1 = row[p].zr;
-                const float2 wx = make_float2(t0.x, t0.y);
-                const float2 wy = make_float2(t0.z, t0.w);
-                const float2 wz = make_float2(t1.x, t1.y);
-                const float2 rjk = make_float2(t1.z, t1.w);
-                float2 p1 = f2_mul(u3x, vx[p]);                // -3 cos t_i
-                p1 = f2_fma(u3y, vy[p], p1);
-                p1 = f2_fma(u3z, vz[p], p1);
-                float2 p2 = f2_mul(ux, wx);                    // -cos t_j
-                p2 = f2_fma(uy, wy, p2);
-                p2 = f2_fma(uz, wz, p2);
-                float2 p3 = f2_mul(vx[p], wx);                 // cos t_k
-                p3 = f2_fma(vy[p], wy, p3);
-                p3 = f2_fma(vz[p], wz, p3);
-                const float2 t = f2_mul(f2_mul(p1, p2), p3);   // 3 cos cos cos
-                const float2 q = f2_fma(t, rjk, rjk);          // (1 + 3 cos cos cos) rho_jk
-                s2 = f2_fma(q, rk[p], s2);                     // row sum (x rho_ij later)
-                acc[p] = f2_fma(q, rij2, acc[p]);              // column sums (x rho_ik later)
-            }
+            const float2 s2 = row_half(&row->xy, &row->zr, 2, vx, vy, vz, rk, acc, ux, uy, uz,
+                                       u3x, u3y, u3z, rij2);
             const float srow = (s2.x + s2.y) * rij;
             acc_i += srow;
             if (half == 0) redJ[jj][lane] = srow;
             else redJ[jj][lane] += srow;
+        }
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+            const float2 c = f2_mul(acc[p], rk[p]);
+            redK[kb + 2 * p][lane] = c.x;
+            redK[kb + 2 * p + 1][lane] = c.y;
+        }
+    }
+    __syncwarp();
+    return acc_i;
+}
+
+// Pair-table block of one tile pair (A, B): 32 x 32 pair terms from particle
+// A*32 + r to B*32 + c, stored as two planes indexed [column pair p][row r],
+// so that a warp whose lanes are rows reads 512 contiguous bytes per plane.
+struct PairBlock {
+    float4 xy[kTile / 2][kTile];  // (ex_c, ex_c+1, ey_c, ey_c+1), c = 2p
+    float4 zr[kTile / 2][kTile];  // (ez_c, ez_c+1, rho_c, rho_c+1)
+};
+
+// The same sweep with every pair term read from a precomputed pair table
+// (unit vector and r^-3 of each pair, computed in FP64 and rounded once to
+// FP32) instead of formed from coordinates:
+//   tab : block (J, K) in shared memory (rows j, columns k)
+//   bIK : block (I, K) in global memory (the lane's row: its (i, k) terms)
+//   bIJ : block (I, J) in global memory (the lane's row: its (i, j) terms)
+// Masked and absent pairs are zero in the table, so no masks are needed here.
+__device__ __forceinline__ float tile_triples_table(const PairBlock& tab,
+                                                    const PairBlock* __restrict__ bIK,
+                                                    const PairBlock* __restrict__ bIJ, int lane,
+                                                    float (*redJ)[kTile + 1],
+                                                    float (*redK)[kTile + 1]) {
+    float acc_i = 0.f;
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const int kb = half * kHalf;
+        float2 vx[kPairs], vy[kPairs], vz[kPairs], rk[kPairs], acc[kPairs];
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+            const float4 a = __ldg(&bIK->xy[(kb >> 1) + p][lane]);
+            const float4 b = __ldg(&bIK->zr[(kb >> 1) + p][lane]);
+            vx[p] = make_float2(a.x, a.y);
+            vy[p] = make_float2(a.z, a.w);
+            vz[p] = make_float2(b.x, b.y);
+            rk[p] = make_float2(b.z, b.w);
+            acc[p] = make_float2(0.f, 0.f);
+        }
+#pragma unroll 1
+        for (int jp = 0; jp < kTile / 2; ++jp) {
+            const float4 cxy = __ldg(&bIJ->xy[jp][lane]), czr = __ldg(&bIJ->zr[jp][lane]);
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int jj = 2 * jp + o;
+                const float ex = o ? cxy.y : cxy.x, ey = o ? cxy.w : cxy.z;
+                const float ez = o ? czr.y : czr.x, rij = o ? czr.w : czr.z;
+                const float2 s2 = row_half(&tab.xy[kb >> 1][jj], &tab.zr[kb >> 1][jj], kTile, vx,
+                                           vy, vz, rk, acc, f2_splat(ex), f2_splat(ey),
+                                           f2_splat(ez), f2_splat(-3.0f * ex),
+                                           f2_splat(-3.0f * ey), f2_splat(-3.0f * ez),
+                                           f2_splat(rij));
+                const float srow = (s2.x + s2.y) * rij;
+                acc_i += srow;
+                if (half == 0) redJ[jj][lane] = srow;
+                else redJ[jj][lane] += srow;
+            }
         }
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {

@@ -73,7 +73,7 @@ def test_small_n_is_zero(mode):
 def test_closed_forms_on_gpu(mode):
     d = 1.7
     tri = np.array([[0, 0, 0], [d, 0, 0], [d / 2, d * np.sqrt(3) / 2, 0]])
-    rt = 1e-12 if mode == "fp64" else TOL["fp32"]
+    rt = 1e-12 if mode == "fp64" else 1e-6
     np.testing.assert_allclose(_gpu(tri, mode), 1.375 / d ** 9, rtol=rt)
     col = np.array([[0, 0, 0], [2 * d, 0, 0], [d, 0, 0]])
     np.testing.assert_allclose(_gpu(col, mode), -0.25 / d ** 9, rtol=rt)
