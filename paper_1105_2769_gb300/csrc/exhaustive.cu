@@ -199,23 +199,25 @@ pair_table_kernel(const double* __restrict__ X, int N, int NT,
 }
 
 struct PtSmem {
-    mbm_tile::PairBlock tab[2];  // (j, k) table of this item and the next
+    mbm_tile::PairBlock tab;            // (j, k) table of the current item
+    mbm_tile::IjRing ring[kWarps32];    // per-warp staging of (i, j) pair terms
     float redJ[kWarps32][kTile][kTile + 1];
     float redK[kWarps32][kTile][kTile + 1];
     double wsum[2][kWarps32][kTile];
-    unsigned long long bar[2];
-    long long item[2];
+    unsigned long long bar;
+    long long item;
 };
 
 // An item's (j, k) table is block (J, K) of the pair table: one 16 KB bulk
-// copy, issued by thread 0 one item ahead.
-__device__ __forceinline__ void issue_item_table(PtSmem& sm, int buf, long long t, int NT,
+// copy, issued by thread 0 as soon as the previous item's warps are done
+// with the buffer.
+__device__ __forceinline__ void issue_item_table(PtSmem& sm, long long t, int NT,
                                                  const mbm_tile::PairBlock* pt) {
     int J, K;
     decode_pair_item(t, NT, J, K);
     const unsigned bytes = (unsigned)sizeof(mbm_tile::PairBlock);
-    mbar_arrive_expect_tx(&sm.bar[buf], bytes);
-    bulk_copy_g2s(&sm.tab[buf], pt + pt_block(J, K, NT), bytes, &sm.bar[buf]);
+    mbar_arrive_expect_tx(&sm.bar, bytes);
+    bulk_copy_g2s(&sm.tab, pt + pt_block(J, K, NT), bytes, &sm.bar);
 }
 
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: a copy that never lands
@@ -228,33 +230,26 @@ exh_fp32_pt_kernel(const mbm_tile::PairBlock* __restrict__ pt, int N, int NT, lo
     PtSmem& sm = *reinterpret_cast<PtSmem*>(smem_raw);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
+    bool pending = false;  // thread 0: a table copy issued and not yet waited for
     if (threadIdx.x == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
+        mbar_init(&sm.bar, 1);
         mbar_fence_init();
         const long long t = (long long)atomicAdd(counter, 1ULL);
-        sm.item[0] = t;
-        if (t < n_items) issue_item_table(sm, 0, t, NT, pt);
+        sm.item = t;
+        if (t < n_items) {
+            issue_item_table(sm, t, NT, pt);
+            pending = true;
+        }
     }
     __syncthreads();
-    unsigned parity[2] = {0u, 0u};
-    bool pending[2] = {sm.item[0] < n_items, false};  // thread 0: copy issued, not yet waited
-    int buf = 0;
+    unsigned parity = 0u;
     for (;;) {
-        const long long t = sm.item[buf];
+        const long long t = sm.item;
         if (t >= n_items) break;
-        if (threadIdx.x == 0) {
-            const long long tn = (long long)atomicAdd(counter, 1ULL);
-            sm.item[buf ^ 1] = tn;
-            if (tn < n_items) {
-                issue_item_table(sm, buf ^ 1, tn, NT, pt);
-                pending[buf ^ 1] = true;
-            }
-        }
-        const bool ok = mbar_wait_bounded(&sm.bar[buf], parity[buf], kWaitCycles);
+        const bool ok = mbar_wait_bounded(&sm.bar, parity, kWaitCycles);
         if (ok) {
-            parity[buf] ^= 1u;
-            pending[buf] = false;
+            parity ^= 1u;
+            pending = false;
         }
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicOr(flags, MBM_FLAG_TIMEOUT);
@@ -272,7 +267,7 @@ exh_fp32_pt_kernel(const mbm_tile::PairBlock* __restrict__ pt, int N, int NT, lo
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(nb + o));
             }
             const float acc_i = mbm_tile::tile_triples_table(
-                sm.tab[buf], pt + pt_block(I, K, NT), pt + pt_block(I, J, NT), lane,
+                sm.tab, pt + pt_block(I, K, NT), pt + pt_block(I, J, NT), lane, sm.ring[warp],
                 sm.redJ[warp], sm.redK[warp]);
             run_j += (double)mbm_tile::row_sum(sm.redJ[warp], lane);
             run_k += (double)mbm_tile::row_sum(sm.redK[warp], lane);
@@ -281,7 +276,15 @@ exh_fp32_pt_kernel(const mbm_tile::PairBlock* __restrict__ pt, int N, int NT, lo
         }
         sm.wsum[0][warp][lane] = run_j;
         sm.wsum[1][warp][lane] = run_k;
-        __syncthreads();
+        __syncthreads();  // every warp is done with the table buffer
+        if (threadIdx.x == 0) {
+            const long long tn = (long long)atomicAdd(counter, 1ULL);
+            sm.item = tn;
+            if (tn < n_items) {
+                issue_item_table(sm, tn, NT, pt);
+                pending = true;
+            }
+        }
         if (warp < 2) {
             double tot = 0.0;
 #pragma unroll
@@ -290,14 +293,10 @@ exh_fp32_pt_kernel(const mbm_tile::PairBlock* __restrict__ pt, int N, int NT, lo
             if (idx < N) atomicAdd(&phi[idx], tot);
         }
         __syncthreads();
-        buf ^= 1;
     }
-    // A copy is still in flight here only after a timed-out wait: give each
-    // one a bounded chance to land before the CTA's shared memory is released.
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < 2; ++b)
-            if (pending[b]) mbar_wait_bounded(&sm.bar[b], parity[b], kWaitCycles);
-    }
+    // A copy is still in flight here only after a timed-out wait: give it a
+    // bounded chance to land before the CTA's shared memory is released.
+    if (threadIdx.x == 0 && pending) mbar_wait_bounded(&sm.bar, parity, kWaitCycles);
 }
 
 // ---------------------------------------------------------------------------

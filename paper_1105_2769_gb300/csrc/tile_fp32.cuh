@@ -203,23 +203,48 @@ struct PairBlock {
     float4 zr[kTile / 2][kTile];  // (ez_c, ez_c+1, rho_c, rho_c+1)
 };
 
+// Per-warp staging ring of the lane's (i, j) pair terms: slot s holds one
+// column pair of the (I, J) block (both planes, 32 lanes).
+struct IjRing {
+    float4 xy[2][kTile];
+    float4 zr[2][kTile];
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_1() {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
 // The same sweep with every pair term read from a precomputed pair table
 // (unit vector and r^-3 of each pair, computed in FP64 and rounded once to
 // FP32) instead of formed from coordinates:
 //   tab : block (J, K) in shared memory (rows j, columns k)
 //   bIK : block (I, K) in global memory (the lane's row: its (i, k) terms)
-//   bIJ : block (I, J) in global memory (the lane's row: its (i, j) terms)
+//   bIJ : block (I, J) in global memory (the lane's row: its (i, j) terms),
+//         staged one column pair ahead through the warp's ring by cp.async
+//         (each lane copies and reads only its own entries)
 // Masked and absent pairs are zero in the table, so no masks are needed here.
 __device__ __forceinline__ float tile_triples_table(const PairBlock& tab,
                                                     const PairBlock* __restrict__ bIK,
                                                     const PairBlock* __restrict__ bIJ, int lane,
-                                                    float (*redJ)[kTile + 1],
+                                                    IjRing& ring, float (*redJ)[kTile + 1],
                                                     float (*redK)[kTile + 1]) {
     float acc_i = 0.f;
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
         const int kb = half * kHalf;
         float2 vx[kPairs], vy[kPairs], vz[kPairs], rk[kPairs], acc[kPairs];
+        cp_async16(&ring.xy[0][lane], &bIJ->xy[0][lane]);
+        cp_async16(&ring.zr[0][lane], &bIJ->zr[0][lane]);
+        cp_async_commit();
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
             const float4 a = __ldg(&bIK->xy[(kb >> 1) + p][lane]);
@@ -232,7 +257,13 @@ __device__ __forceinline__ float tile_triples_table(const PairBlock& tab,
         }
 #pragma unroll 1
         for (int jp = 0; jp < kTile / 2; ++jp) {
-            const float4 cxy = __ldg(&bIJ->xy[jp][lane]), czr = __ldg(&bIJ->zr[jp][lane]);
+            if (jp + 1 < kTile / 2) {
+                cp_async16(&ring.xy[(jp + 1) & 1][lane], &bIJ->xy[jp + 1][lane]);
+                cp_async16(&ring.zr[(jp + 1) & 1][lane], &bIJ->zr[jp + 1][lane]);
+            }
+            cp_async_commit();
+            cp_async_wait_1();  // this column pair's copies have landed
+            const float4 cxy = ring.xy[jp & 1][lane], czr = ring.zr[jp & 1][lane];
 #pragma unroll
             for (int o = 0; o < 2; ++o) {
                 const int jj = 2 * jp + o;
