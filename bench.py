@@ -41,10 +41,10 @@ WORKLOAD = "exh32_n32768"
 N_MAIN = 32768
 FLOPS_PER_TRIPLE_FP32 = 23   # counted from the inner loop (FMA = 2), see csrc/tile_fp32.cuh
 FP32_LANES_PER_SM = 128
-# dram__bytes_read.sum + dram__bytes_write.sum of one exh_fp32_kernel launch on
+# dram__bytes_read.sum + dram__bytes_write.sum of one exh_fp32_pt_kernel launch on
 # the N = 32 768 set (ncu, one pass; the command is in
 # profiles/exh_fp32_n32768_launches.md). Valid for the kernel as committed with it.
-EXH_FP32_TRAFFIC_BYTES = 2100480
+EXH_FP32_TRAFFIC_BYTES = 4088735832064 + 14698218240
 N_CONFIG3 = 1 << 20
 
 
@@ -431,10 +431,14 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops,
                 "traffic": EXH_FP32_TRAFFIC_BYTES if len(X) == N_MAIN else None,
-                "traffic_note": "ncu dram bytes per launch (read 2 100 480, write 0)",
+                "traffic_note": ("ncu dram bytes per launch of the sweep (read 4.089e12, write "
+                                 "1.47e10): it streams the pair table's (i,k) blocks, 16 B per "
+                                 "pair term (0.7 B per triple), by design: the table replaces "
+                                 "FP32 pair set-up in the sweep; algorithmic input+output is "
+                                 "1.0 MB"),
                 "peak_note": (f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 "
                               f"x {sm_max:.0f} MHz (maximum SM clock)"),
-                "kernel": "exh_fp32_kernel", "flops_per_triple": FLOPS_PER_TRIPLE_FP32,
+                "kernel": "exh_fp32_pt_kernel", "flops_per_triple": FLOPS_PER_TRIPLE_FP32,
                 "kernel_ms": k_ms}
     if clocks.get("sm_mhz"):
         roofline["frac_at_sampled_clock"] = achieved / (peak_tflops * clocks["sm_mhz"] / sm_max)

@@ -157,6 +157,11 @@ static void at_grad_first(const double* xi, const double* xj, const double* xk,
     if (phi_out) *phi_out = phi;
 }
 
+/* d phi(x_i, x_j, x_k) / d x_i at one triple (the tree-forces oracle's step). */
+void oracle_at_grad(const double* xi, const double* xj, const double* xk, double* g) {
+    at_grad_first(xi, xj, xk, g, NULL);
+}
+
 /* Gradient of E with respect to x_i for each requested i (forces are -grad). */
 int oracle_grad(const double* X, int64_t N, const int64_t* idx, int64_t n_idx,
                 double* out3, double* normout, int nthreads) {

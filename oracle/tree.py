@@ -29,7 +29,11 @@ def bind_trace(L):
     L.oracle_mc_draw.argtypes = [vp, vp, vp, ctypes.c_int, i64, vp, i64, vp]
     L.oracle_tree_potential_trace.argtypes = [vp, i64, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int,
                                               dbl, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
-                                              vp, vp, vp, i64, vp, vp, vp, vp, vp, i64, vp]
+                                              ctypes.c_int, vp, vp, vp, i64, vp, vp, vp, vp, vp,
+                                              i64, vp]
+    if hasattr(L, "oracle_tree_forces"):
+        L.oracle_tree_forces.argtypes = [vp, i64, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int, dbl,
+                                         ctypes.c_uint64, ctypes.c_int, vp, vp, vp]
 
 
 def _lib():
@@ -63,25 +67,29 @@ def tree_potential(X, eps=0.0, tau=0.0, alpha=0.0, leaf_size=32, m_limit=256, ze
 
 def tree_potential_trace(X, eps=0.0, tau=0.0, alpha=0.0, leaf_size=32, m_limit=256, zeta=32.0,
                          seed=0x5eed5eed, mc_rule=0, seed_up=3, cap_tri=1 << 16, cap_mc=1 << 18,
-                         lib=None):
-    """tree_potential plus the record of every prune: returns (Phi, stats, trace) with
-    trace = {"kind", "P" (node triples), "mc_tri", "mc_pt", "mc_mean", "mc_sig", "mc_m"}.
-    `lib` may name another compiled copy of the oracle (planted-mistake tests)."""
+                         lib=None, forces=False):
+    """tree_potential (or, with forces=True, tree_forces) plus the record of every
+    prune: returns (result, stats, trace) with trace = {"kind", "P" (node triples),
+    "mc_tri", "mc_pt", "mc_mean", "mc_sig", "mc_m"} (mean and sigma: 3 per point
+    for forces). `lib` may name another compiled copy of the oracle (planted-mistake
+    tests)."""
     L = lib if lib is not None else _lib()
     X = np.ascontiguousarray(X, dtype=np.float64)
     n = len(X)
-    out = np.zeros(n)
+    dim = 3 if forces else 1
+    out = np.zeros(n * dim)
     stats = np.zeros(6, dtype=np.int64)
     tri = np.zeros((cap_tri, 4), dtype=np.int64)
     mc_tri = np.zeros(cap_mc, dtype=np.int64)
     mc_pt = np.zeros(cap_mc, dtype=np.int64)
     mc_m = np.zeros(cap_mc, dtype=np.int64)
-    mc_mean = np.zeros(cap_mc)
-    mc_sig = np.zeros(cap_mc)
+    mc_mean = np.zeros(cap_mc * dim)
+    mc_sig = np.zeros(cap_mc * dim)
     n_out = np.zeros(2, dtype=np.int64)
     rc = L.oracle_tree_potential_trace(_p(X), n, float(eps), float(tau), float(alpha),
                                        int(leaf_size), int(m_limit), float(zeta), int(seed),
-                                       int(mc_rule), int(seed_up), _p(out), _p(stats), _p(tri),
+                                       int(mc_rule), int(seed_up), int(dim == 3), _p(out),
+                                       _p(stats), _p(tri),
                                        cap_tri, _p(mc_tri), _p(mc_pt), _p(mc_mean), _p(mc_sig),
                                        _p(mc_m), cap_mc, _p(n_out))
     if rc != 0:
@@ -91,9 +99,31 @@ def tree_potential_trace(X, eps=0.0, tau=0.0, alpha=0.0, leaf_size=32, m_limit=2
         raise RuntimeError(f"trace capacity exceeded ({nt} prunes, {nm} Monte Carlo points)")
     keys = ["visited", "det_prunes", "mc_prunes", "mc_attempts", "base_cases", "mc_samples"]
     trace = {"kind": tri[:nt, 0].copy(), "P": tri[:nt, 1:].copy(), "mc_tri": mc_tri[:nm],
-             "mc_pt": mc_pt[:nm], "mc_mean": mc_mean[:nm], "mc_sig": mc_sig[:nm],
-             "mc_m": mc_m[:nm]}
+             "mc_pt": mc_pt[:nm], "mc_mean": mc_mean[:nm * dim].reshape(nm, dim).squeeze(),
+             "mc_sig": mc_sig[:nm * dim].reshape(nm, dim).squeeze(), "mc_m": mc_m[:nm]}
+    if dim == 3:
+        out = out.reshape(n, 3)
+        trace["mc_mean"] = trace["mc_mean"].reshape(-1, 3)
+        trace["mc_sig"] = trace["mc_sig"].reshape(-1, 3)
     return out, dict(zip(keys, stats.tolist())), trace
+
+
+def tree_forces(X, eps=0.0, tau=0.0, alpha=0.0, leaf_size=32, m_limit=256, zeta=32.0,
+                seed=0x5eed5eed, seed_up=3, with_counts=False):
+    """Serial restatement of the tree forces (force criterion of tree_oracle.c);
+    returns (F (N x 3), counts, stats)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    n = len(X)
+    out = np.zeros((n, 3))
+    counts = np.zeros(n, dtype=np.int64) if with_counts else None
+    stats = np.zeros(6, dtype=np.int64)
+    rc = _lib().oracle_tree_forces(_p(X), n, float(eps), float(tau), float(alpha), int(leaf_size),
+                                   int(m_limit), float(zeta), int(seed), int(seed_up), _p(out),
+                                   _p(counts) if with_counts else None, _p(stats))
+    if rc != 0:
+        raise RuntimeError("oracle_tree_forces failed")
+    keys = ["visited", "det_prunes", "mc_prunes", "mc_attempts", "base_cases", "mc_samples"]
+    return out, counts, dict(zip(keys, stats.tolist()))
 
 
 def mc_draw(P, begin, end, slot, x, r, lib=None):

@@ -86,6 +86,8 @@ typedef struct {
     double* diam2;     /* squared bbox diagonal */
     double* phil;      /* Phi^l per node */
     double* pphil;     /* Phi^l per sorted point, |S(x)| */
+    double* nscale;    /* forces: A^l per node (min over its points) */
+    double* pscale;    /* forces: A^l per sorted point */
 } otree;
 
 static uint64_t spread3(uint32_t v) {
@@ -181,6 +183,7 @@ static void tree_build(const double* X, int64_t N, int leaf_size, otree* t) {
 static void tree_free(otree* t) {
     free(t->perm); free(t->Xs); free(t->begin); free(t->end); free(t->lo);
     free(t->hi); free(t->cen); free(t->diam2); free(t->phil); free(t->pphil);
+    free(t->nscale); free(t->pscale);
 }
 
 static inline int64_t node_n(const otree* t, int64_t v) { return t->end[v] - t->begin[v]; }
@@ -198,7 +201,7 @@ typedef struct {
     int64_t cap_mc, n_mc;
     int64_t* mc_tri;
     int64_t* mc_pt;
-    double* mc_mean;
+    double* mc_mean;   /* dim per entry: 1 (potential) or 3 (forces) */
     double* mc_sig;
     int64_t* mc_m;
 } otrace;
@@ -216,6 +219,10 @@ typedef struct {
     int64_t* pt_cnt;
     int64_t det_prunes, mc_prunes, mc_attempts, base_cases, visited, mc_samples;
     otrace* trace;      /* optional */
+    int forces;         /* 1: tree forces (node_acc3, pt_acc3, force rules) */
+    double* node_acc3;  /* 3 per node */
+    double* pt_acc3;    /* 3 per sorted point, Neumaier-compensated by pt_cmp3 */
+    double* pt_cmp3;
 } osolve;
 
 static int64_t trace_prune(osolve* S, int kind, const int64_t P[3]) {
@@ -422,7 +429,13 @@ static void pt_add(osolve* S, int64_t p, double x) {
     S->pt_acc[p] = t;
 }
 
+static void base_case_forces(osolve* S, const int64_t P[3]);
+
 static void base_case(osolve* S, const int64_t P[3]) {
+    if (S->forces) {
+        base_case_forces(S, P);
+        return;
+    }
     const otree* t = S->t;
     int e01 = P[0] == P[1], e12 = P[1] == P[2];
     for (int64_t i = t->begin[P[0]]; i < t->end[P[0]]; ++i)
@@ -440,7 +453,10 @@ static void base_case(osolve* S, const int64_t P[3]) {
 
 static void recurse(osolve* S, int64_t P1, int64_t P2, int64_t P3);
 
+static int try_summarize_forces(osolve* S, const int64_t P[3]);
+
 static int try_summarize(osolve* S, const int64_t P[3]) {
+    if (S->forces) return try_summarize_forces(S, P);
     const otree* t = S->t;
     double n[3] = {(double)node_n(t, P[0]), (double)node_n(t, P[1]), (double)node_n(t, P[2])};
     double T[3];
@@ -557,6 +573,252 @@ static void recurse(osolve* S, int64_t P1, int64_t P2, int64_t P3) {
     }
 }
 
+
+/* ======================= tree forces (no counterpart in the paper) =======================
+ * F(x) = -sum over the tuples {y, z} containing x of grad_x phi(x, y, z), the
+ * negative gradient of the total energy. The recursion is Algorithm 2 with
+ * the same splits; the value a prune credits and the rules that allow it are
+ * those of the force error criterion (one component d at a time)
+ *     |F~_d(x) - F_d(x)| <= eps S(x) + tau,
+ *     S(x) = sum over the tuples containing x of |grad_x phi|_2,
+ * a sum of magnitudes, which cancelling terms cannot shrink.
+ *   seed  : A^l(x) = the same sum over the tuples inside x's seed node, a
+ *           lower bound of S(x) (non-negative terms over a subset of the
+ *           tuples); A^l(P) = min over P's points.
+ *   p = 0 : with u, v the edges at slot s and the pair-vector form of the
+ *           gradient, |grad_x phi|_2 <= 3R/r_u (|5t-1| + 2) + 3R/r_v (|5t-1| + 2)
+ *           <= 18 R_max (1/d^l_u + 1/d^l_v) = M_s over all point triples of
+ *           the boxes (|5t - 1| <= 4 because the cosine product lies in
+ *           [-1, 1/8]); crediting T_s grad phi(c1, c2, c3) to slot s errs by at
+ *           most 2 M_s per tuple and component, so a triple is summarized iff
+ *           2 M_s <= (eps A^l(P_s) + tau) / T^root for every distinct slot.
+ *   MC    : Algorithm 4 with the three components of grad_x phi as the
+ *           sample; a point passes iff z sigma_d <= (eps A^l(x) + tau)/T^root
+ *           for d = 1, 2, 3 (sigma_d from the (m - 1) sample variance).
+ * Every credit is -T times a gradient (a force), pushed top-down like the
+ * potential's node accumulators.
+ */
+void oracle_at_grad(const double* xi, const double* xj, const double* xk, double* g);
+
+static double grad_norm(const double* xi, const double* xj, const double* xk) {
+    double g[3];
+    oracle_at_grad(xi, xj, xk, g);
+    return sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+}
+
+/* A^l: exact sum of |grad_x phi|_2 over the tuples inside each point's seed node */
+static void seed_scale(otree* t, int seed_up) {
+    int64_t N = t->N;
+    t->pscale = (double*)calloc((size_t)N, sizeof(double));
+    int sd = t->depth - seed_up;
+    if (sd < 0) sd = 0;
+    int64_t first = ((int64_t)1 << sd) - 1;
+    for (int64_t q = 0; q < ((int64_t)1 << sd); ++q) {
+        int64_t v = first + q, b = t->begin[v], e = t->end[v];
+        int64_t p;
+#pragma omp parallel for schedule(dynamic, 8)
+        for (p = b; p < e; ++p) {
+            double acc = 0.0, cmp = 0.0;
+            for (int64_t y = b; y < e; ++y) {
+                if (y == p) continue;
+                for (int64_t z = y + 1; z < e; ++z) {
+                    if (z == p) continue;
+                    double f = grad_norm(t->Xs + 3 * p, t->Xs + 3 * y, t->Xs + 3 * z);
+                    double s2 = acc + f;
+                    cmp += fabs(acc) >= f ? (acc - s2) + f : (f - s2) + acc;
+                    acc = s2;
+                }
+            }
+            t->pscale[p] = acc + cmp;
+        }
+    }
+    t->nscale = (double*)malloc(sizeof(double) * (size_t)t->n_nodes);
+    for (int64_t v = 0; v < t->n_nodes; ++v) {
+        double m = INFINITY;
+        for (int64_t p = t->begin[v]; p < t->end[v]; ++p) if (t->pscale[p] < m) m = t->pscale[p];
+        t->nscale[v] = t->begin[v] < t->end[v] ? m : 0.0;
+    }
+}
+
+static void pt_add3(osolve* S, int64_t p, const double g[3], double sgn) {
+    for (int d = 0; d < 3; ++d) {
+        double a = S->pt_acc3[3 * p + d], x = sgn * g[d], t2 = a + x;
+        if (fabs(a) >= fabs(x)) S->pt_cmp3[3 * p + d] += (a - t2) + x;
+        else S->pt_cmp3[3 * p + d] += (x - t2) + a;
+        S->pt_acc3[3 * p + d] = t2;
+    }
+}
+
+/* gradient of phi with respect to the point of slot s of (a0, a1, a2) */
+static void grad_slot(const double* a0, const double* a1, const double* a2, int s, double g[3]) {
+    if (s == 0) oracle_at_grad(a0, a1, a2, g);
+    else if (s == 1) oracle_at_grad(a1, a0, a2, g);
+    else oracle_at_grad(a2, a0, a1, g);
+}
+
+static void base_case_forces(osolve* S, const int64_t P[3]) {
+    const otree* t = S->t;
+    int e01 = P[0] == P[1], e12 = P[1] == P[2];
+    for (int64_t i = t->begin[P[0]]; i < t->end[P[0]]; ++i)
+        for (int64_t j = t->begin[P[1]]; j < t->end[P[1]]; ++j) {
+            if (e01 && j <= i) continue;
+            for (int64_t k = t->begin[P[2]]; k < t->end[P[2]]; ++k) {
+                if (e12 && k <= j) continue;
+                const double *a = t->Xs + 3 * i, *b = t->Xs + 3 * j, *c = t->Xs + 3 * k;
+                double g[3];
+                grad_slot(a, b, c, 0, g); pt_add3(S, i, g, -1.0);
+                grad_slot(a, b, c, 1, g); pt_add3(S, j, g, -1.0);
+                grad_slot(a, b, c, 2, g); pt_add3(S, k, g, -1.0);
+                if (S->pt_cnt) { S->pt_cnt[i]++; S->pt_cnt[j]++; S->pt_cnt[k]++; }
+            }
+        }
+    S->base_cases++;
+}
+
+/* Algorithm 4 for point x with the gradient as a 3-component sample; returns 1
+ * if the point passes, its force estimate -T_i mu in est[3] and mu, sigma_mu
+ * (3 each) and the sample count in mus[0..6]. */
+static int mc_point_forces(osolve* S, const int64_t P[3], int slot, int64_t x, double Ti,
+                           double ascale, double est[3], double mus[7]) {
+    const otree* t = S->t;
+    double mean[3] = {0, 0, 0}, m2[3] = {0, 0, 0}, sig[3] = {0, 0, 0};
+    int m = 0, pass = 0;
+    uint32_t r[4] = {0, 0, 0, 0};
+    const double rhs = (S->eps * ascale + S->tau) * (1.0 / S->troot);
+    for (;;) {
+        if ((m & 1) == 0) {
+            int c = m >> 1;
+            uint32_t ctr[4] = {(uint32_t)x, (uint32_t)P[0] | ((uint32_t)(c & 0xFF) << 24),
+                               (uint32_t)P[1] | ((uint32_t)((c >> 8) & 0xFF) << 24), (uint32_t)P[2]};
+            oracle_philox4x32_10(ctr, S->key, r);
+        }
+        int64_t y, z;
+        draw_partners(S, P, slot, x, (m & 1) ? r[2] : r[0], (m & 1) ? r[3] : r[1], &y, &z);
+        double g[3];
+        oracle_at_grad(t->Xs + 3 * x, t->Xs + 3 * y, t->Xs + 3 * z, g);
+        ++m;
+        for (int d = 0; d < 3; ++d) {
+            double dlt = g[d] - mean[d];
+            mean[d] += dlt * (1.0 / (double)m);
+            m2[d] += dlt * (g[d] - mean[d]);
+        }
+        if (m >= 2 && (m >= 30 || m >= S->m_limit)) {
+            pass = 1;
+            for (int d = 0; d < 3; ++d) {
+                sig[d] = sqrt(m2[d] * (1.0 / (double)(m - 1)) * (1.0 / (double)m));
+                if (!(S->z * sig[d] <= rhs)) pass = 0;
+            }
+            if ((pass && m >= 30) || m >= S->m_limit) break;
+        } else if (m >= S->m_limit) {
+            pass = 0;
+            break;
+        }
+    }
+    S->mc_samples += m;
+    for (int d = 0; d < 3; ++d) {
+        est[d] = -Ti * mean[d];
+        mus[d] = mean[d];
+        mus[3 + d] = sig[d];
+    }
+    mus[6] = (double)m;
+    return pass;
+}
+
+static int try_summarize_forces(osolve* S, const int64_t P[3]) {
+    const otree* t = S->t;
+    double n[3] = {(double)node_n(t, P[0]), (double)node_n(t, P[1]), (double)node_n(t, P[2])};
+    double T[3];
+    for (int s = 0; s < 3; ++s) T[s] = tuples_for_slot(P, n, s);
+    int first[3] = {1, P[1] != P[0], P[2] != P[1]};
+    /* ---- deterministic p = 0 rule for the gradient ---- */
+    double sl[3], sh[3];
+    box_d2(t, P[0], P[1], &sl[0], &sh[0]);
+    box_d2(t, P[0], P[2], &sl[1], &sh[1]);
+    box_d2(t, P[1], P[2], &sl[2], &sh[2]);
+    if (sl[0] > 0.0 && sl[1] > 0.0 && sl[2] > 0.0) {
+        double prod = sl[0] * sl[1] * sl[2];
+        double rmax = 1.0 / (prod * sqrt(prod));
+        double inv[3] = {1.0 / sqrt(sl[0]), 1.0 / sqrt(sl[1]), 1.0 / sqrt(sl[2])};
+        /* edges at each slot: slot 0 -> (0-1, 0-2), slot 1 -> (0-1, 1-2), slot 2 -> (0-2, 1-2) */
+        double M[3] = {18.0 * rmax * (inv[0] + inv[1]), 18.0 * rmax * (inv[0] + inv[2]),
+                       18.0 * rmax * (inv[1] + inv[2])};
+        int ok = 1;
+        for (int s = 0; s < 3; ++s) {
+            if (!first[s]) continue;
+            double budget = (S->eps * t->nscale[P[s]] + S->tau) / S->troot;
+            if (!(2.0 * M[s] <= budget)) ok = 0;
+        }
+        if (ok) {
+            const double *c0 = t->cen + 3 * P[0], *c1 = t->cen + 3 * P[1], *c2 = t->cen + 3 * P[2];
+            for (int s = 0; s < 3; ++s) {
+                if (!first[s]) continue;
+                double g[3];
+                grad_slot(c0, c1, c2, s, g);
+                for (int d = 0; d < 3; ++d) S->node_acc3[3 * P[s] + d] += -T[s] * g[d];
+                if (S->node_cnt) S->node_cnt[P[s]] += (int64_t)T[s];
+            }
+            S->det_prunes++;
+            trace_prune(S, 0, P);
+            return 1;
+        }
+    }
+    /* ---- Monte Carlo rule (Algorithm 3) ---- */
+    if (S->alpha > 0.0) {
+        double tmin = T[0];
+        for (int s = 1; s < 3; ++s) if (T[s] < tmin) tmin = T[s];
+        if (tmin >= 1.0 && S->zeta * S->m_limit <= tmin) {
+            S->mc_attempts++;
+            int64_t total = 0;
+            for (int s = 0; s < 3; ++s) if (first[s]) total += node_n(t, P[s]);
+            double* est = (double*)malloc(sizeof(double) * 3 * (size_t)total);
+            double* mus = (double*)malloc(sizeof(double) * 7 * (size_t)total);
+            int64_t q = 0;
+            int ok = 1;
+            for (int s = 0; s < 3 && ok; ++s) {
+                if (!first[s]) continue;
+                for (int64_t x = t->begin[P[s]]; x < t->end[P[s]]; ++x) {
+                    if (!mc_point_forces(S, P, s, x, T[s], t->pscale[x], est + 3 * q,
+                                         mus + 7 * q)) {
+                        ok = 0;
+                        break;
+                    }
+                    ++q;
+                }
+            }
+            if (ok) { /* Algorithm 5 */
+                int64_t k = trace_prune(S, 1, P);
+                q = 0;
+                for (int s = 0; s < 3; ++s) {
+                    if (!first[s]) continue;
+                    for (int64_t x = t->begin[P[s]]; x < t->end[P[s]]; ++x) {
+                        if (S->trace) {
+                            otrace* tr = S->trace;
+                            int64_t e = tr->n_mc++;
+                            if (e < tr->cap_mc) {
+                                tr->mc_tri[e] = k;
+                                tr->mc_pt[e] = x;
+                                for (int d = 0; d < 3; ++d) {
+                                    tr->mc_mean[3 * e + d] = mus[7 * q + d];
+                                    tr->mc_sig[3 * e + d] = mus[7 * q + 3 + d];
+                                }
+                                tr->mc_m[e] = (int64_t)mus[7 * q + 6];
+                            }
+                        }
+                        pt_add3(S, x, est + 3 * q, 1.0);
+                        ++q;
+                        if (S->pt_cnt) S->pt_cnt[x] += (int64_t)T[s];
+                    }
+                }
+                S->mc_prunes++;
+            }
+            free(est);
+            free(mus);
+            if (ok) return 1;
+        }
+    }
+    return 0;
+}
+
 int oracle_phi(const double* X, int64_t N, const int64_t* idx, int64_t n_idx, double* out,
                double* absout, int nthreads);
 
@@ -593,29 +855,38 @@ static void seed_phil(otree* t, int seed_up) {
  *   stats (optional, int64[6]): visited, det prunes, MC prunes, MC attempts,
  *   base cases, MC samples.
  */
-static int tree_potential(const double* X, int64_t N, double eps, double tau, double alpha,
-                          int leaf_size, int m_limit, double zeta, uint64_t seed, int mc_rule,
-                          int seed_up, double* out, int64_t* counts, int64_t* stats,
-                          otrace* trace) {
+static int tree_solve(const double* X, int64_t N, double eps, double tau, double alpha,
+                      int leaf_size, int m_limit, double zeta, uint64_t seed, int mc_rule,
+                      int seed_up, int forces, double* out, int64_t* counts, int64_t* stats,
+                      otrace* trace) {
+    const int dim = forces ? 3 : 1;
     if (N < 3) {
-        for (int64_t i = 0; i < N; ++i) { out[i] = 0.0; if (counts) counts[i] = 0; }
+        for (int64_t i = 0; i < N * dim; ++i) out[i] = 0.0;
+        for (int64_t i = 0; i < N; ++i) if (counts) counts[i] = 0;
         return 0;
     }
     otree t;
     tree_build(X, N, leaf_size, &t);
-    seed_phil(&t, seed_up);
+    if (forces) seed_scale(&t, seed_up);
+    else seed_phil(&t, seed_up);
     osolve S;
     memset(&S, 0, sizeof(S));
     S.t = &t;
     S.eps = eps; S.tau = tau; S.alpha = alpha; S.zeta = zeta;
     S.m_limit = m_limit; S.mc_rule = mc_rule;
     S.trace = trace;
+    S.forces = forces;
     S.troot = choose2((double)(N - 1));
     S.z = oracle_z_two_sided(alpha);
     S.key[0] = (uint32_t)seed; S.key[1] = (uint32_t)(seed >> 32);
     S.node_acc = (double*)calloc((size_t)t.n_nodes, sizeof(double));
     S.pt_acc = (double*)calloc((size_t)N, sizeof(double));
     S.pt_cmp = (double*)calloc((size_t)N, sizeof(double));
+    if (forces) {
+        S.node_acc3 = (double*)calloc(3 * (size_t)t.n_nodes, sizeof(double));
+        S.pt_acc3 = (double*)calloc(3 * (size_t)N, sizeof(double));
+        S.pt_cmp3 = (double*)calloc(3 * (size_t)N, sizeof(double));
+    }
     if (counts) {
         S.node_cnt = (int64_t*)calloc((size_t)t.n_nodes, sizeof(int64_t));
         S.pt_cnt = (int64_t*)calloc((size_t)N, sizeof(int64_t));
@@ -626,13 +897,20 @@ static int tree_potential(const double* X, int64_t N, double eps, double tau, do
         if (v > 0) {
             int64_t par = (v - 1) / 2;
             S.node_acc[v] += S.node_acc[par];
+            if (forces)
+                for (int d = 0; d < 3; ++d) S.node_acc3[3 * v + d] += S.node_acc3[3 * par + d];
             if (counts) S.node_cnt[v] += S.node_cnt[par];
         }
     }
     int64_t lf = t.n_nodes - t.n_leaves;
     for (int64_t v = lf; v < t.n_nodes; ++v)
         for (int64_t p = t.begin[v]; p < t.end[v]; ++p) {
-            out[t.perm[p]] = (S.pt_acc[p] + S.pt_cmp[p]) + S.node_acc[v];
+            if (forces)
+                for (int d = 0; d < 3; ++d)
+                    out[3 * t.perm[p] + d] = (S.pt_acc3[3 * p + d] + S.pt_cmp3[3 * p + d]) +
+                                             S.node_acc3[3 * v + d];
+            else
+                out[t.perm[p]] = (S.pt_acc[p] + S.pt_cmp[p]) + S.node_acc[v];
             if (counts) counts[t.perm[p]] = S.pt_cnt[p] + S.node_cnt[v];
         }
     if (stats) {
@@ -640,6 +918,7 @@ static int tree_potential(const double* X, int64_t N, double eps, double tau, do
         stats[3] = S.mc_attempts; stats[4] = S.base_cases; stats[5] = S.mc_samples;
     }
     free(S.node_acc); free(S.pt_acc); free(S.pt_cmp);
+    free(S.node_acc3); free(S.pt_acc3); free(S.pt_cmp3);
     if (counts) { free(S.node_cnt); free(S.pt_cnt); }
     tree_free(&t);
     return 0;
@@ -648,18 +927,31 @@ static int tree_potential(const double* X, int64_t N, double eps, double tau, do
 int oracle_tree_potential(const double* X, int64_t N, double eps, double tau, double alpha,
                           int leaf_size, int m_limit, double zeta, uint64_t seed, int mc_rule,
                           int seed_up, double* out, int64_t* counts, int64_t* stats) {
-    return tree_potential(X, N, eps, tau, alpha, leaf_size, m_limit, zeta, seed, mc_rule, seed_up,
-                          out, counts, stats, NULL);
+    return tree_solve(X, N, eps, tau, alpha, leaf_size, m_limit, zeta, seed, mc_rule, seed_up, 0,
+                      out, counts, stats, NULL);
 }
 
-/* The same solve, recording every prune (see otrace) into caller buffers:
- * tri (4 x cap_tri int64), and per Monte Carlo point mc_tri, mc_pt, mc_m
- * (int64) and mc_mean, mc_sig (double), cap_mc entries each. n_out[0..1]
+/*
+ * Tree approximation of the forces F = -grad E (3 per particle, original
+ * order) under the force criterion above; arguments as oracle_tree_potential
+ * (no mc_rule: the force stop test has one form).
+ */
+int oracle_tree_forces(const double* X, int64_t N, double eps, double tau, double alpha,
+                       int leaf_size, int m_limit, double zeta, uint64_t seed, int seed_up,
+                       double* out3, int64_t* counts, int64_t* stats) {
+    return tree_solve(X, N, eps, tau, alpha, leaf_size, m_limit, zeta, seed, 0, seed_up, 1, out3,
+                      counts, stats, NULL);
+}
+
+/* The same solve (forces = 0) or the tree forces (forces = 1, out has 3 per
+ * particle), recording every prune (see otrace) into caller buffers: tri
+ * (4 x cap_tri int64), and per Monte Carlo point mc_tri, mc_pt, mc_m (int64)
+ * and mc_mean, mc_sig (1 or 3 doubles each), cap_mc entries. n_out[0..1]
  * receive the number of prunes and of Monte Carlo point entries (which may
  * exceed the capacities; entries past them are not written). */
 int oracle_tree_potential_trace(const double* X, int64_t N, double eps, double tau, double alpha,
                                 int leaf_size, int m_limit, double zeta, uint64_t seed,
-                                int mc_rule, int seed_up, double* out, int64_t* stats,
+                                int mc_rule, int seed_up, int forces, double* out, int64_t* stats,
                                 int64_t* tri, int64_t cap_tri, int64_t* mc_tri, int64_t* mc_pt,
                                 double* mc_mean, double* mc_sig, int64_t* mc_m, int64_t cap_mc,
                                 int64_t* n_out) {
@@ -668,8 +960,8 @@ int oracle_tree_potential_trace(const double* X, int64_t N, double eps, double t
     tr.cap_tri = cap_tri; tr.tri = tri;
     tr.cap_mc = cap_mc; tr.mc_tri = mc_tri; tr.mc_pt = mc_pt;
     tr.mc_mean = mc_mean; tr.mc_sig = mc_sig; tr.mc_m = mc_m;
-    int rc = tree_potential(X, N, eps, tau, alpha, leaf_size, m_limit, zeta, seed, mc_rule,
-                            seed_up, out, NULL, stats, &tr);
+    int rc = tree_solve(X, N, eps, tau, alpha, leaf_size, m_limit, zeta, seed, mc_rule, seed_up,
+                        forces, out, NULL, stats, &tr);
     n_out[0] = tr.n_tri;
     n_out[1] = tr.n_mc;
     return rc;
