@@ -206,10 +206,28 @@ mbm_status mbm_tree_export(const mbm_tree* tree, int64_t* perm_dev, double* lo_d
  * Forces F_i = -dE/dx_i of the total energy E = sum_{a<b<c} phi_abc
  * (no counterpart in the paper; the derivative of Eq. 1's summand).
  *   F_dev : N x 3 FP64 device array, written.
- *   mode  : MBM_EXH_FP64 or MBM_EXH_FP32 (tree forces: MBM_ENOTSUP).
+ *   mode  : MBM_EXH_FP64 or MBM_EXH_FP32 (exhaustive adjoint), or MBM_TREE[|MBM_ABS]:
+ *           the multi-tree recursion (Algorithm 2's traversal and splits)
+ *           under a force criterion, since the paper bounds potentials only:
+ *           every component of F_i within eps S_i + tau, where
+ *           S_i = sum over the tuples containing i of |grad_i phi|_2 (a sum of
+ *           magnitudes, which cancelling terms cannot shrink); MBM_ABS makes
+ *           eps the absolute tau. A pruned node triple credits
+ *           -T_s grad_s phi(c1, c2, c3) (p = 0: pruned when 2 M_s <=
+ *           (eps A^l + tau)/T^root with M_s a bound on |grad phi| over the
+ *           boxes and A^l <= S the exact sum over the seed node) or, with
+ *           alpha > 0, a Monte Carlo mean (Algorithms 3-5 with the three
+ *           components as the sample); base cases are exact.
  */
 mbm_status mbm_forces(mbm_ctx* ctx, const double* X_dev, int64_t N, double eps, double alpha,
                       int mode, double* F_dev, mbm_stream_t stream);
+
+/* As mbm_forces, with explicit configuration (NULL = defaults), an optional
+ * prebuilt tree for MBM_TREE (NULL = build one) and an optional stats record
+ * (NULL = not reported; filling it synchronises). */
+mbm_status mbm_forces_ex(mbm_ctx* ctx, const double* X_dev, int64_t N, double eps, double alpha,
+                         int mode, const mbm_config* cfg, mbm_tree* tree, double* F_dev,
+                         mbm_stats* stats, mbm_stream_t stream);
 
 /*
  * Vector-Jacobian product of Phi: gradX_m = d/dx_m sum_l g_l Phi(x_l)
@@ -259,7 +277,7 @@ enum { MBM_REQ_POTENTIAL = 0, MBM_REQ_FORCES = 1 };
 
 typedef struct {
     int32_t kind;          /* MBM_REQ_POTENTIAL or MBM_REQ_FORCES */
-    int32_t mode;          /* MBM_EXH_FP32 / MBM_EXH_FP64 / MBM_TREE[|MBM_ABS] (tree: potential) */
+    int32_t mode;          /* MBM_EXH_FP32 / MBM_EXH_FP64 / MBM_TREE[|MBM_ABS] (both kinds) */
     int64_t N;
     const double* X_host;  /* N x 3 FP64, caller-owned, read while the request runs */
     double* out_host;      /* N (potential) or N x 3 (forces) FP64, caller-owned, written */

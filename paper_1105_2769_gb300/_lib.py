@@ -90,6 +90,8 @@ SIGNATURES = {
     "mbm_potential_host": (_int, [_vp, _vp, _i64, _dbl, _dbl, _int, ctypes.POINTER(Config),
                                   _vp, _vp]),
     "mbm_forces": (_int, [_vp, _vp, _i64, _dbl, _dbl, _int, _vp, _vp]),
+    "mbm_forces_ex": (_int, [_vp, _vp, _i64, _dbl, _dbl, _int, ctypes.POINTER(Config), _vp, _vp,
+                             ctypes.POINTER(Stats), _vp]),
     "mbm_potential_vjp": (_int, [_vp, _vp, _i64, _vp, _int, _vp, _vp]),
     "mbm_potential_fp32_noalloc": (_int, [_vp, _i64, _vp, _vp]),
     "mbm_tree_build": (_int, [_vp, _vp, _i64, ctypes.POINTER(Config), _vp, ctypes.POINTER(_vp)]),

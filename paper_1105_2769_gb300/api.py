@@ -209,15 +209,25 @@ def potential_sampled(X: torch.Tensor, idx, ctx: Context | None = None) -> torch
 
 
 def forces(X: torch.Tensor, mode="fp32", eps: float = 0.0, alpha: float = 0.0,
-           ctx: Context | None = None) -> torch.Tensor:
-    """F_i = -dE/dx_i, E = sum over unordered triples of phi."""
+           ctx: Context | None = None, config: _lib.Config | None = None, tree=None,
+           stats: bool = False, tuple_counts: torch.Tensor | None = None):
+    """F_i = -dE/dx_i, E = sum over unordered triples of phi: exhaustive
+    ("fp32", "fp64") or tree-approximated ("tree", "tree_abs": every component
+    within eps S_i + tau, S_i the sum of |grad_i phi| over the tuples)."""
     X = _check_points(X)
     ctx = ctx or default_context(X.device.index)
     F = torch.empty_like(X)
-    _lib.check(_lib.load().mbm_forces(ctx.handle, ctypes.c_void_p(X.data_ptr()), X.shape[0],
-                                      float(eps), float(alpha), _mode(mode),
-                                      ctypes.c_void_p(F.data_ptr()), _stream_handle()))
-    return F
+    cfg = config if config is not None else _lib.default_config()
+    if tuple_counts is not None:
+        cfg = _lib.Config.from_buffer_copy(cfg)
+        cfg.tuple_counts = tuple_counts.data_ptr()
+    st = _lib.Stats()
+    _lib.check(_lib.load().mbm_forces_ex(ctx.handle, ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                         float(eps), float(alpha), _mode(mode), ctypes.byref(cfg),
+                                         tree.handle if tree is not None else None,
+                                         ctypes.c_void_p(F.data_ptr()),
+                                         ctypes.byref(st) if stats else None, _stream_handle()))
+    return (F, st.as_dict()) if stats else F
 
 
 def potential_vjp(X: torch.Tensor, g: torch.Tensor, mode="fp32",

@@ -21,8 +21,11 @@
 //   forces: F_i = -sum_{j<k} grad_i phi(i,j,k)      (weights 1)
 // Inner loop (per lane-triple, FP32): 9 (dots) + 4 (A1, t, A2, A3) + 1 (q)
 // + 2 (R) + 1 (W) + 2 (s_u, s_v) + 6 (c1, c2, c3) + 5 (sums) = 30 operations.
+#include <cstring>
+
 #include "device_math.cuh"
 #include "mbm_internal.h"
+#include "mbm_tree_api.h"
 
 namespace {
 
@@ -337,18 +340,42 @@ mbm_status run_adjoint(mbm_ctx* ctx, const double* X, int64_t N, const double* g
 
 }  // namespace
 
-extern "C" mbm_status mbm_forces(mbm_ctx* ctx, const double* X_dev, int64_t N, double eps,
-                                 double alpha, int mode, double* F_dev, mbm_stream_t stream) {
-    (void)eps;
-    (void)alpha;
+extern "C" mbm_status mbm_forces_ex(mbm_ctx* ctx, const double* X_dev, int64_t N, double eps,
+                                    double alpha, int mode, const mbm_config* cfg, mbm_tree* tree,
+                                    double* F_dev, mbm_stats* stats, mbm_stream_t stream) {
     if (!ctx) return mbm_fail(MBM_EINVAL, "ctx is NULL");
     if (N < 0) return mbm_fail(MBM_EINVAL, "N < 0");
     if (N > 0 && (!X_dev || !F_dev)) return mbm_fail(MBM_EINVAL, "NULL X or output");
+    if (!(eps >= 0.0)) return mbm_fail(MBM_EINVAL, "eps must be >= 0");
+    if (!(alpha >= 0.0 && alpha < 1.0)) return mbm_fail(MBM_EINVAL, "alpha must be in [0, 1)");
+    const int base_mode = mode & 0xff;
+    if (base_mode != MBM_EXH_FP64 && base_mode != MBM_EXH_FP32 && base_mode != MBM_TREE)
+        return mbm_fail(MBM_EINVAL, "unknown mode");
+    if ((mode & ~0x1ff) != 0 || ((mode & MBM_ABS) && base_mode != MBM_TREE))
+        return mbm_fail(MBM_EINVAL, "unknown mode flags");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    mbm_config c;
+    if (cfg) c = *cfg;
+    else mbm_config_default(&c);
     std::lock_guard<std::mutex> lock(ctx->mu);
     MBM_CUDA_TRY(cudaSetDevice(ctx->device));
     if (N == 0) return MBM_OK;
-    return run_adjoint(ctx, X_dev, N, nullptr, mode, F_dev, -1.0,
-                       reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (base_mode == MBM_TREE) {
+        if (N < 3) {
+            MBM_CUDA_TRY(cudaMemsetAsync(F_dev, 0, (size_t)N * 3 * sizeof(double), s));
+            return MBM_OK;
+        }
+        return mbm_tree_forces(ctx, X_dev, N, eps, alpha, (mode & MBM_ABS) != 0, c, tree, F_dev,
+                               stats, s);
+    }
+    return run_adjoint(ctx, X_dev, N, nullptr, mode, F_dev, -1.0, s);
+}
+
+extern "C" mbm_status mbm_forces(mbm_ctx* ctx, const double* X_dev, int64_t N, double eps,
+                                 double alpha, int mode, double* F_dev, mbm_stream_t stream) {
+    return mbm_forces_ex(ctx, X_dev, N, eps, alpha, mode, nullptr, nullptr, F_dev, nullptr,
+                         stream);
 }
 
 extern "C" mbm_status mbm_potential_vjp(mbm_ctx* ctx, const double* X_dev, int64_t N,

@@ -79,7 +79,7 @@ size_t estimate_bytes(const mbm_request& r, const mbm_config& c) {
     const size_t io = N * 24 + N * (r.kind == MBM_REQ_FORCES ? 24 : 8);
     const int base = r.mode & 0xff;
     if (base != MBM_TREE) return io + N * 32 + 4096;
-    return io + mbm_tree_solve_bytes(r.N, c) + (1 << 20);
+    return io + mbm_tree_solve_bytes(r.N, c, r.kind == MBM_REQ_FORCES) + (1 << 20);
 }
 
 }  // namespace
@@ -172,7 +172,8 @@ mbm_status solve_job(Worker& w, const Job& job, const double* X, mbm_tree* tree,
     mbm_stream_t ms = reinterpret_cast<mbm_stream_t>(w.stream);
     stamp_kernel<<<1, 1, 0, w.stream>>>(w.d_stamp);
     mbm_status st;
-    if (r.kind == MBM_REQ_FORCES) st = mbm_forces(w.ctx, X, r.N, r.eps, r.alpha, r.mode, w.dOut, ms);
+    if (r.kind == MBM_REQ_FORCES)
+        st = mbm_forces_ex(w.ctx, X, r.N, r.eps, r.alpha, r.mode, &job.cfg, tree, w.dOut, nullptr, ms);
     else st = mbm_potential_ex(w.ctx, X, r.N, r.eps, r.alpha, r.mode, &job.cfg, tree, w.dOut, nullptr, ms);
     stamp_kernel<<<1, 1, 0, w.stream>>>(w.d_stamp + 1);
     if (st != MBM_OK) return st;

@@ -604,6 +604,10 @@ struct Trav {
     int64_t cap_base;
     int* flags;
     ull* stat;  // visited, det, mc prunes, mc attempts, base, samples
+    // tree forces only
+    const double *nscale, *pscale;  // A^l per node (min) and per sorted particle
+    double* node_acc3;              // 3 per node
+    double* pt_acc3;                // 3 per sorted particle
 };
 
 __device__ __forceinline__ bool is_leaf(const Trav& p, int64_t v) {
@@ -702,6 +706,51 @@ __device__ double phi_f64(const double* x, const double* y, const double* z) {
     return (S + 0.375 * P) / (S * S * sqrt(S));
 }
 
+// d phi(a, b, c) / d a in FP64 (pair-vector form): with u = b - a, v = c - a,
+// w = c - b, unit vectors e, p1 = e_u.e_v, p2 = e_u.e_w, p3 = e_v.e_w,
+// t = p1 p2 p3 and R = (r_u r_v r_w)^-3,
+//   grad = -g_u - g_v,  g_u = 3R/r_u (q e_u - p2 p3 e_v - p1 p3 e_w),
+//   g_v = 3R/r_v (q e_v - p2 p3 e_u - p1 p2 e_w),  q = 5t - 1.
+__device__ void grad_first_f64(const double* a, const double* b, const double* c, double g[3]) {
+    double u[3], v[3], w[3];
+    for (int k = 0; k < 3; ++k) {
+        u[k] = b[k] - a[k];
+        v[k] = c[k] - a[k];
+        w[k] = c[k] - b[k];
+    }
+    const double ru = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double rv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const double rw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double p1 = 0.0, p2 = 0.0, p3 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        u[k] /= ru;
+        v[k] /= rv;
+        w[k] /= rw;
+    }
+    for (int k = 0; k < 3; ++k) {
+        p1 += u[k] * v[k];
+        p2 += u[k] * w[k];
+        p3 += v[k] * w[k];
+    }
+    const double rr = ru * rv * rw;
+    const double R3 = 3.0 / (rr * rr * rr);
+    const double q = 5.0 * p1 * p2 * p3 - 1.0;
+    const double su = R3 / ru, sv = R3 / rv;
+    for (int k = 0; k < 3; ++k) {
+        const double gu = su * (q * u[k] - p2 * p3 * v[k] - p1 * p3 * w[k]);
+        const double gv = sv * (q * v[k] - p2 * p3 * u[k] - p1 * p2 * w[k]);
+        g[k] = -gu - gv;
+    }
+}
+
+// The gradient with respect to the point of slot s of (a0, a1, a2).
+__device__ void grad_slot_f64(const double* a0, const double* a1, const double* a2, int s,
+                              double g[3]) {
+    if (s == 0) grad_first_f64(a0, a1, a2, g);
+    else if (s == 1) grad_first_f64(a1, a0, a2, g);
+    else grad_first_f64(a2, a0, a1, g);
+}
+
 // Warp-aggregated append: returns this lane's first slot.
 __device__ __forceinline__ ull warp_append(ull* counter, int count) {
     const int lane = threadIdx.x & 31;
@@ -775,6 +824,11 @@ __device__ void triple_counts(const Trav& p, const int64_t P[3], double n[3], do
 
 enum : int { kActNone = 0, kActDet = 1, kActMC = 2, kActBase = 3, kActSplit = 4 };
 
+// F = false: the potential (p = 0 interval of phi, credit T_i phi(c1, c2, c3)).
+// F = true : the forces (bound M_s on |grad phi|_2 over the boxes, prune iff
+//            2 M_s <= (eps A^l(P_s) + tau) / T^root for every distinct slot;
+//            credit -T_s grad_s phi(c1, c2, c3)).
+template <bool F>
 __global__ void classify_kernel(const int4* __restrict__ front, int64_t n_front, Trav p) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int act = kActNone;
@@ -794,7 +848,27 @@ __global__ void classify_kernel(const int4* __restrict__ front, int64_t n_front,
         // Touching boxes (d^l = 0, e.g. a repeated node) leave phi_hi = +inf:
         // the width is infinite and the rule cannot prune; skip its arithmetic.
         bool prune = false;
-        if (sl[0] > 0.0 && sl[1] > 0.0 && sl[2] > 0.0) {
+        if (F) {
+            if (sl[0] > 0.0 && sl[1] > 0.0 && sl[2] > 0.0) {
+                const double prod = __dmul_rn(__dmul_rn(sl[0], sl[1]), sl[2]);
+                const double rmax = __ddiv_rn(1.0, __dmul_rn(prod, __dsqrt_rn(prod)));
+                const double i0 = __ddiv_rn(1.0, __dsqrt_rn(sl[0]));
+                const double i1 = __ddiv_rn(1.0, __dsqrt_rn(sl[1]));
+                const double i2 = __ddiv_rn(1.0, __dsqrt_rn(sl[2]));
+                const double r18 = __dmul_rn(18.0, rmax);
+                // edges at slot 0: (0-1, 0-2); slot 1: (0-1, 1-2); slot 2: (0-2, 1-2)
+                const double M[3] = {__dmul_rn(r18, __dadd_rn(i0, i1)),
+                                     __dmul_rn(r18, __dadd_rn(i0, i2)),
+                                     __dmul_rn(r18, __dadd_rn(i1, i2))};
+                prune = true;
+                for (int s2 = 0; s2 < 3; ++s2) {
+                    if (!first[s2]) continue;
+                    const double budget = __ddiv_rn(
+                        __dadd_rn(__dmul_rn(p.eps, p.nscale[P[s2]]), p.tau), p.troot);
+                    if (!(__dmul_rn(2.0, M[s2]) <= budget)) prune = false;
+                }
+            }
+        } else if (sl[0] > 0.0 && sl[1] > 0.0 && sl[2] > 0.0) {
             double plo, phi_hi;
             phi_interval(sl[0], sh[0], sl[1], sh[1], sl[2], sh[2], plo, phi_hi);
             const double width = __dsub_rn(phi_hi, plo);
@@ -811,11 +885,21 @@ __global__ void classify_kernel(const int4* __restrict__ front, int64_t n_front,
         }
         if (prune) {
             act = kActDet;
-            const double f = phi_f64(p.ncen + 3 * P[0], p.ncen + 3 * P[1], p.ncen + 3 * P[2]);
-            for (int s = 0; s < 3; ++s) {
-                if (!first[s]) continue;
-                atomicAdd(&p.node_acc[P[s]], T[s] * f);
-                if (p.node_cnt) atomicAdd(&p.node_cnt[P[s]], (ull)T[s]);
+            if (F) {
+                for (int s = 0; s < 3; ++s) {
+                    if (!first[s]) continue;
+                    double g[3];
+                    grad_slot_f64(p.ncen + 3 * P[0], p.ncen + 3 * P[1], p.ncen + 3 * P[2], s, g);
+                    for (int d = 0; d < 3; ++d) atomicAdd(&p.node_acc3[3 * P[s] + d], -T[s] * g[d]);
+                    if (p.node_cnt) atomicAdd(&p.node_cnt[P[s]], (ull)T[s]);
+                }
+            } else {
+                const double f = phi_f64(p.ncen + 3 * P[0], p.ncen + 3 * P[1], p.ncen + 3 * P[2]);
+                for (int s = 0; s < 3; ++s) {
+                    if (!first[s]) continue;
+                    atomicAdd(&p.node_acc[P[s]], T[s] * f);
+                    if (p.node_cnt) atomicAdd(&p.node_cnt[P[s]], (ull)T[s]);
+                }
             }
         } else {
             double tmin = T[0];
@@ -1094,6 +1178,122 @@ __device__ double mc_warp(const Trav& p, const int64_t P[3], const int64_t bb[3]
     return __dmul_rn(Ti, mean);
 }
 
+
+// Unit vector, r^-3 and r^-1 of one pair (as pair_sample).
+struct PairFY {
+    float ex, ey, ez, rho, y;
+};
+__device__ __forceinline__ PairFY pair_sample_y(float4 ph, float4 pl, float4 qh, float4 ql) {
+    const float dx = (qh.x - ph.x) + (ql.x - pl.x);
+    const float dy = (qh.y - ph.y) + (ql.y - pl.y);
+    const float dz = (qh.z - ph.z) + (ql.z - pl.z);
+    const float s = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    float y = rsqrtf(s);
+    y = fmaf(0.5f * y, fmaf(-s * y, y, 1.0f), y);
+    PairFY r;
+    r.ex = dx * y;
+    r.ey = dy * y;
+    r.ez = dz * y;
+    r.y = y;
+    r.rho = y * y * y;
+    return r;
+}
+
+// grad_a phi(a, b, c) in FP32 bulk (pair-vector form, as grad_first_f64),
+// from hi/lo coordinates of a, b and c.
+__device__ __forceinline__ float3 grad_first_fp32(float4 ah, float4 al, float4 bh, float4 bl,
+                                                  float4 ch, float4 cl) {
+    const PairFY ab = pair_sample_y(ah, al, bh, bl);
+    const PairFY ac = pair_sample_y(ah, al, ch, cl);
+    const PairFY bc = pair_sample_y(bh, bl, ch, cl);
+    const float p1 = ab.ex * ac.ex + ab.ey * ac.ey + ab.ez * ac.ez;
+    const float p2 = ab.ex * bc.ex + ab.ey * bc.ey + ab.ez * bc.ez;
+    const float p3 = ac.ex * bc.ex + ac.ey * bc.ey + ac.ez * bc.ez;
+    const float q = fmaf(5.0f, p1 * p2 * p3, -1.0f);
+    const float R3 = 3.0f * (ab.rho * ac.rho * bc.rho);
+    const float su = R3 * ab.y, sv = R3 * ac.y;  // 3R / r_ab, 3R / r_ac
+    const float p23 = p2 * p3, p13 = p1 * p3, p12 = p1 * p2;
+    float3 g;
+    g.x = -su * (q * ab.ex - p23 * ac.ex - p13 * bc.ex) - sv * (q * ac.ex - p23 * ab.ex - p12 * bc.ex);
+    g.y = -su * (q * ab.ey - p23 * ac.ey - p13 * bc.ey) - sv * (q * ac.ey - p23 * ab.ey - p12 * bc.ey);
+    g.z = -su * (q * ab.ez - p23 * ac.ez - p13 * bc.ez) - sv * (q * ac.ez - p23 * ab.ez - p12 * bc.ez);
+    return g;
+}
+
+// Algorithm 4 for the forces: the sample is the three components of
+// grad_x phi(x, y, z); a particle passes iff z sigma_d <= rhs for d = 1..3 with
+// rhs = (eps A^l(x) + tau) / T^root (the force criterion). Same draws, counts
+// and early stops as mc_warp. Writes the estimate -T_i mu to est[3].
+__device__ void mc_warp_forces(const Trav& p, const int64_t P[3], const int64_t bb[3],
+                               const int64_t nn[3], bool active, int slot, int64_t x, double Ti,
+                               volatile int* fail, double est[3]) {
+    const int lane = threadIdx.x & 31;
+    const double scale = active ? p.pscale[x] : 0.0;
+    const double rhs = __dmul_rn(__dadd_rn(__dmul_rn(p.eps, scale), p.tau), p.inv_troot);
+    const double reject_v = __dmul_rn(__dmul_rn(rhs, rhs) / (p.z * p.z), 1.0 + 1e-9);
+    const double hopeless_m2 =
+        __dmul_rn(__dmul_rn(reject_v, (double)(p.m_limit - 1) * (double)p.m_limit), 1.0 + 1e-9);
+    double mean[3] = {0.0, 0.0, 0.0}, m2[3] = {0.0, 0.0, 0.0};
+    int m = 0;
+    bool pass = false, done = !active;
+    int samples = 0, iter = 0;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 xh0 = active ? p.xh[x] : z4, xl0 = active ? p.xl[x] : z4;
+    auto step = [&](float3 g) {
+        ++m;
+        ++samples;
+        const double gv[3] = {(double)g.x, (double)g.y, (double)g.z};
+        double m2max = 0.0, mmax = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double dlt = __dsub_rn(gv[d], mean[d]);
+            mean[d] = __fma_rn(dlt, p.rcp[m], mean[d]);
+            m2[d] = __fma_rn(dlt, __dsub_rn(gv[d], mean[d]), m2[d]);
+            m2max = fmax(m2max, m2[d]);
+            mmax = fmax(mmax, fabs(mean[d]));
+        }
+        const bool testing = m >= 2 && (m >= 30 || m >= p.m_limit);
+        if (m >= 2 && m2max > hopeless_m2 && m2max > hopeless_m2 + 1e-20 * mmax * mmax) {
+            pass = false;  // no later m can pass (m2 never decreases)
+            done = true;
+        } else if (testing) {
+            pass = true;
+            for (int d = 0; d < 3; ++d) {
+                const double sig = __dsqrt_rn(__dmul_rn(__dmul_rn(m2[d], p.rcp[m - 1]), p.rcp[m]));
+                if (!(__dmul_rn(p.z, sig) <= rhs)) pass = false;
+            }
+            if ((pass && m >= 30) || m >= p.m_limit) done = true;
+        } else if (m >= p.m_limit) {
+            pass = false;
+            done = true;
+        }
+        if (done && !pass) *fail = 1;
+    };
+    while (__any_sync(0xffffffffu, !done)) {
+        if (!done) {
+            const int c = m >> 1;
+            const uint32_t ctr1 = (uint32_t)P[0] | ((uint32_t)(c & 0xFF) << 24);
+            const uint32_t ctr2 = (uint32_t)P[1] | ((uint32_t)((c >> 8) & 0xFF) << 24);
+            uint32_t rr[4];
+            philox4x32_10((uint32_t)x, ctr1, ctr2, (uint32_t)P[2], p.key0, p.key1, rr);
+            int64_t y0, z0, y1, z1;
+            draw_partners(P, bb, nn, slot, x, rr[0], rr[1], y0, z0);
+            draw_partners(P, bb, nn, slot, x, rr[2], rr[3], y1, z1);
+            const float3 g0 = grad_first_fp32(xh0, xl0, p.xh[y0], p.xl[y0], p.xh[z0], p.xl[z0]);
+            const float3 g1 = grad_first_fp32(xh0, xl0, p.xh[y1], p.xl[y1], p.xh[z1], p.xl[z1]);
+            step(g0);
+            if (!done) step(g1);
+        }
+        if ((++iter & 15) == 0) {
+            int f = lane == 0 ? *fail : 0;
+            if (__shfl_sync(0xffffffffu, f, 0)) break;
+        }
+    }
+    int tot = samples;
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0 && tot) atomicAdd(&p.stat[5], (ull)tot);
+    for (int d = 0; d < 3; ++d) est[d] = -__dmul_rn(Ti, mean[d]);
+}
+
 __device__ __forceinline__ void candidate_geometry(const Trav& p, const int64_t P[3], double T[3],
                                                    bool first[3], int64_t bb[3], int64_t nn[3],
                                                    int64_t& U) {
@@ -1112,6 +1312,7 @@ __device__ __forceinline__ void candidate_geometry(const Trav& p, const int64_t 
 // likeliest to fail) run first, a warp per candidate: 32, 16 or 10 of them
 // per node for 1, 2 or 3 distinct nodes, so the lanes are filled. A particle's
 // draws depend only on its own ids, so decisions do not depend on this order.
+template <bool F>
 __global__ void mc_probe_kernel(const int4* __restrict__ mc, int64_t n_c, int* cand_fail, Trav p) {
     const int lane = threadIdx.x & 31;
     const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -1130,7 +1331,12 @@ __global__ void mc_probe_kernel(const int4* __restrict__ mc, int64_t n_c, int* c
     const int q = lane / per;
     const int slot = q < d ? ds[q] : 0;
     const int x = q < d ? p.weak[P[slot] * 32 + (lane % per)] : -1;
-    mc_warp(p, P, bb, nn, x >= 0, slot, x >= 0 ? x : 0, T[slot], fail);
+    if (F) {
+        double e3[3];
+        mc_warp_forces(p, P, bb, nn, x >= 0, slot, x >= 0 ? x : 0, T[slot], fail, e3);
+    } else {
+        mc_warp(p, P, bb, nn, x >= 0, slot, x >= 0 ? x : 0, T[slot], fail);
+    }
 }
 
 __global__ void mc_sizes_kernel(const int4* __restrict__ mc, int64_t n_mc, int64_t N,
@@ -1153,7 +1359,9 @@ __global__ void mc_sizes_kernel(const int4* __restrict__ mc, int64_t n_mc, int64
     chunks[c] = (U + 31) / 32;
 }
 
-// One warp per 32-particle chunk of a candidate that passed the probe.
+// One warp per 32-particle chunk of a candidate that passed the probe
+// (forces: 3 estimates per particle).
+template <bool F>
 __global__ void mc_kernel(const int4* __restrict__ mc, int64_t c0, int64_t n_c,
                           const int64_t* __restrict__ chunk_off /* exclusive, n_c + 1 */,
                           int* cand_fail, double* est, Trav p) {
@@ -1181,11 +1389,19 @@ __global__ void mc_kernel(const int4* __restrict__ mc, int64_t c0, int64_t n_c,
     int slot = 0;
     int64_t x = 0;
     if (active) candidate_point(p, P, u, slot, x);
-    const double e = mc_warp(p, P, bb, nn, active, slot, x, T[slot], fail);
-    if (active) est[rel * 32 + lane] = e;
+    if (F) {
+        double e3[3];
+        mc_warp_forces(p, P, bb, nn, active, slot, x, T[slot], fail, e3);
+        if (active)
+            for (int d = 0; d < 3; ++d) est[3 * (rel * 32 + lane) + d] = e3[d];
+    } else {
+        const double e = mc_warp(p, P, bb, nn, active, slot, x, T[slot], fail);
+        if (active) est[rel * 32 + lane] = e;
+    }
 }
 
 // Algorithm 5 for passing candidates; failing ones go on to base/split.
+template <bool F>
 __global__ void mc_commit_kernel(const int4* __restrict__ mc, int64_t c0, int64_t n_c,
                                  const int64_t* __restrict__ chunk_off, const int* cand_fail,
                                  const double* est, Trav p) {
@@ -1204,7 +1420,12 @@ __global__ void mc_commit_kernel(const int4* __restrict__ mc, int64_t c0, int64_
             int slot;
             int64_t x;
             candidate_point(p, P, u, slot, x);
-            atomicAdd(&p.pt_acc[x], est[chunk_off[c] * 32 + u - chunk_off[0] * 32]);
+            const int64_t eo = chunk_off[c] * 32 + u - chunk_off[0] * 32;
+            if (F) {
+                for (int d = 0; d < 3; ++d) atomicAdd(&p.pt_acc3[3 * x + d], est[3 * eo + d]);
+            } else {
+                atomicAdd(&p.pt_acc[x], est[eo]);
+            }
             if (p.pt_cnt) atomicAdd(&p.pt_cnt[x], (ull)T[slot]);
         }
         if (threadIdx.x == 0) atomicAdd(&p.stat[2], 1ULL);
@@ -1258,6 +1479,131 @@ __global__ void finalize_kernel(int64_t N, int depth, int64_t n_nodes, int64_t n
     }
     out[perm[s]] = pt_acc[s] + acc;
     if (counts_out) counts_out[perm[s]] = (int64_t)(cnt + pt_cnt[s]);
+}
+
+// ---------------------------------------------------------------------------
+// Tree forces: seed of the force scale, base cases, top-down push.
+// ---------------------------------------------------------------------------
+// A^l(x) = sum over the tuples inside x's seed node of |grad_x phi|_2, a warp
+// per 32-particle chunk of a seed node (all lanes read the same partners).
+__global__ void __launch_bounds__(128)
+seed_scale_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_t N, int sd,
+                  int chunks_per_node, double* __restrict__ scale) {
+    const int lane = threadIdx.x & 31;
+    const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_nodes = (int64_t)1 << sd;
+    if (item >= n_nodes * chunks_per_node) return;
+    int64_t b, e;
+    node_range(n_nodes - 1 + item / chunks_per_node, N, b, e);
+    const int64_t x = b + (item % chunks_per_node) * 32 + lane;
+    if (b + (item % chunks_per_node) * 32 >= e) return;  // warp-uniform
+    const bool act = x < e;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 ah = act ? xh[x] : z4, al = act ? xl[x] : z4;
+    double acc = 0.0;
+    for (int64_t y = b; y < e; ++y) {
+        const float4 bh = xh[y], bl = xl[y];
+        float row = 0.f;
+        for (int64_t z = y + 1; z < e; ++z) {
+            const float3 g = grad_first_fp32(ah, al, bh, bl, xh[z], xl[z]);
+            const float n2 = fmaf(g.z, g.z, fmaf(g.y, g.y, g.x * g.x));
+            row += (y != x && z != x) ? sqrtf(n2) : 0.f;
+        }
+        acc += (double)row;
+    }
+    if (act) scale[x] = acc;
+}
+
+// Exact forces of base cases (Fig. 4 leaf triples), a warp per item: for each
+// distinct slot, a lane per particle of that leaf sums grad over the partner
+// pairs the canonical case allows, and credits -grad.
+constexpr int kForceWarps = 4;
+__global__ void __launch_bounds__(kForceWarps * 32)
+base_forces_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_t N,
+                   const int4* __restrict__ items, int64_t n_items, double* __restrict__ acc3) {
+    __shared__ float4 sh[kForceWarps][3][kTile], sl[kForceWarps][3][kTile];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (item >= n_items) return;
+    const int4 t = items[item];
+    const int L[3] = {t.x, t.y, t.z};
+    int64_t b[3];
+    int n[3];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < 3; ++s) {
+        int64_t e;
+        node_range(L[s], N, b[s], e);
+        n[s] = (int)(e - b[s]);
+        sh[w][s][lane] = lane < n[s] ? xh[b[s] + lane] : z4;
+        sl[w][s][lane] = lane < n[s] ? xl[b[s] + lane] : z4;
+    }
+    __syncwarp();
+    for (int s = 0; s < 3; ++s) {
+        if (s > 0 && L[s] == L[s - 1]) continue;
+        const int o1 = s == 0 ? 1 : 0, o2 = s == 2 ? 1 : 2;
+        const bool same = L[o1] == L[o2];
+        const bool ex1 = L[o1] == L[s], ex2 = L[o2] == L[s];
+        const float4 ah = sh[w][s][lane], al = sl[w][s][lane];
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int bi = 0; bi < n[o1]; ++bi) {
+            float rx = 0.f, ry = 0.f, rz = 0.f;
+            const bool skip_b = ex1 && bi == lane;
+            for (int ci = same ? bi + 1 : 0; ci < n[o2]; ++ci) {
+                if (skip_b || (ex2 && ci == lane)) continue;
+                const float3 g = grad_first_fp32(ah, al, sh[w][o1][bi], sl[w][o1][bi],
+                                                 sh[w][o2][ci], sl[w][o2][ci]);
+                rx += g.x;
+                ry += g.y;
+                rz += g.z;
+            }
+            gx += (double)rx;
+            gy += (double)ry;
+            gz += (double)rz;
+        }
+        if (lane < n[s]) {
+            const int64_t a = b[s] + lane;
+            atomicAdd(&acc3[3 * a], -gx);
+            atomicAdd(&acc3[3 * a + 1], -gy);
+            atomicAdd(&acc3[3 * a + 2], -gz);
+        }
+    }
+}
+
+// Top-down push of the force accumulators and output in the caller's order.
+__global__ void finalize3_kernel(int64_t N, int depth, int64_t n_nodes, int64_t n_leaves,
+                                 const int64_t* __restrict__ perm, const double* __restrict__ pt3,
+                                 const double* __restrict__ node3, const ull* pt_cnt,
+                                 const ull* node_cnt, double* out3, int64_t* counts_out) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    int64_t q = (s << depth) / N;
+    const int64_t first_leaf = n_nodes - n_leaves;
+    int64_t b, e;
+    node_range(first_leaf + q, N, b, e);
+    while (b > s) {
+        --q;
+        node_range(first_leaf + q, N, b, e);
+    }
+    while (e <= s) {
+        ++q;
+        node_range(first_leaf + q, N, b, e);
+    }
+    int64_t v = first_leaf + q;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    ull cnt = 0;
+    for (;;) {
+        a0 += node3[3 * v];
+        a1 += node3[3 * v + 1];
+        a2 += node3[3 * v + 2];
+        if (node_cnt) cnt += node_cnt[v];
+        if (v == 0) break;
+        v = (v - 1) / 2;
+    }
+    const int64_t o = perm[s];
+    out3[3 * o] = pt3[3 * s] + a0;
+    out3[3 * o + 1] = pt3[3 * s + 1] + a1;
+    out3[3 * o + 2] = pt3[3 * s + 2] + a2;
+    if (counts_out) counts_out[o] = (int64_t)(cnt + pt_cnt[s]);
 }
 
 // Two-sided normal quantile: z with P(|Z| > z) = alpha, bisection on erfc.
@@ -1319,7 +1665,7 @@ struct TravPlan {
     std::vector<size_t> parts;
 };
 
-TravPlan trav_plan(int64_t N, int depth, const mbm_config& cfg) {
+TravPlan trav_plan(int64_t N, int depth, const mbm_config& cfg, bool forces) {
     const int m_limit = cfg.m_limit;
     const bool counting = cfg.tuple_counts != nullptr;
     TravPlan q;
@@ -1362,10 +1708,12 @@ TravPlan trav_plan(int64_t N, int depth, const mbm_config& cfg) {
         (size_t)q.max_levels * q.cap_lvl * 16,                             // level buffers
         (size_t)q.cap_mc * 16, cb * 16,                                    // mc, base
         (size_t)(q.cap_mc + 2) * 8, (size_t)q.cap_mc * 4,                  // chunk_off, fail
-        (size_t)q.cap_est * 8, 256, q.cub_bytes,                           // est, counters
+        (size_t)q.cap_est * (forces ? 24 : 8), 256, q.cub_bytes,           // est, counters
         (size_t)(m_limit + 1) * 8,                                         // 1/m table
         cb * 8, cb * 8, cb * 4, cb * 4,                                    // base keys, x
-        (cb + 1) * 4, (cb + 1) * 4, (cb + 1) * 4, 64, q.sort_bytes};       // flag pos heads
+        (cb + 1) * 4, (cb + 1) * 4, (cb + 1) * 4, 64, q.sort_bytes,        // flag pos heads
+        forces ? (size_t)N * 24 : 0, forces ? (size_t)n_nodes * 24 : 0,    // pt_acc3 node_acc3
+        forces ? (size_t)N * 8 : 0, forces ? (size_t)n_nodes * 8 : 0};     // pscale nscale
     return q;
 }
 
@@ -1583,9 +1931,12 @@ struct Timer {
 
 }  // namespace
 
-mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double eps, double alpha,
-                              bool absolute, const mbm_config& cfg, mbm_tree* tree_in, double* phi,
-                              mbm_stats* stats, cudaStream_t s) {
+// One traversal of Algorithm 2 for the potential (F = false, out: N) or the
+// forces (F = true, out: 3 N; the force criterion of classify_kernel<true>).
+template <bool F>
+static mbm_status tree_solve(mbm_ctx* ctx, const double* X, int64_t N, double eps, double alpha,
+                             bool absolute, const mbm_config& cfg, mbm_tree* tree_in, double* phi,
+                             mbm_stats* stats, cudaStream_t s) {
     if (cfg.m_limit < 2 || cfg.m_limit > 65535) return mbm_fail(MBM_EINVAL, "m_limit must be in [2, 65535]");
     if (!(cfg.zeta >= 0.0)) return mbm_fail(MBM_EINVAL, "zeta must be >= 0");
     if (!(cfg.tau >= 0.0)) return mbm_fail(MBM_EINVAL, "tau must be >= 0");
@@ -1611,7 +1962,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
 
     const int64_t n_nodes = tree->n_nodes, n_leaves = tree->n_leaves;
     const bool counting = cfg.tuple_counts != nullptr;
-    const TravPlan plan = trav_plan(N, tree->depth, cfg);
+    const TravPlan plan = trav_plan(N, tree->depth, cfg, F);
     const int64_t B = plan.B, cap_lvl = plan.cap_lvl, cap_mc = plan.cap_mc;
     const int64_t cap_base = plan.cap_base, cap_est = plan.cap_est;
     const int max_levels = plan.max_levels;
@@ -1631,7 +1982,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
     int4* basel = sc.take<int4>(cap_base);
     int64_t* chunk_off = sc.take<int64_t>(cap_mc + 2);
     int* cand_fail = sc.take<int>(cap_mc);
-    double* est = sc.take<double>(cap_est);
+    double* est = sc.take<double>(cap_est * (F ? 3 : 1));
     ull* ctr = sc.take<ull>(32);  // 0 n_next, 1 n_mc, 2 n_base, 3.. statistics
     void* cub_tmp = sc.take<char>(cub_bytes);
     double* rcp = sc.take<double>(cfg.m_limit + 1);
@@ -1644,6 +1995,10 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
     int* bheads = sc.take<int>(cap_base + 1);
     int* bmeta = sc.take<int>(16);  // 0 n_pieces, 1 piece counter
     void* sort_tmp = sc.take<char>(sort_bytes);
+    double* pt_acc3 = F ? sc.take<double>(3 * N) : nullptr;
+    double* node_acc3 = F ? sc.take<double>(3 * n_nodes) : nullptr;
+    double* pscale = F ? sc.take<double>(N) : nullptr;
+    double* nscale = F ? sc.take<double>(n_nodes) : nullptr;
     ull* h = reinterpret_cast<ull*>(ctx->h_flags) + 8;  // pinned, after the status word
     {
         std::vector<double> r(cfg.m_limit + 1, 0.0);
@@ -1661,6 +2016,24 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         MBM_CUDA_TRY(cudaMemsetAsync(node_cnt, 0, (size_t)n_nodes * 8, s));
     }
     MBM_CUDA_TRY(cudaMemsetAsync(ctr, 0, 32 * sizeof(ull), s));
+    if (F) {
+        MBM_CUDA_TRY(cudaMemsetAsync(pt_acc3, 0, (size_t)N * 24, s));
+        MBM_CUDA_TRY(cudaMemsetAsync(node_acc3, 0, (size_t)n_nodes * 24, s));
+        // A^l: exact sum of |grad_x phi|_2 over each particle's seed node
+        // (the tree's seed level), min per node bottom-up.
+        const int sd = std::max(0, tree->depth - tree->seed_levels);
+        const int64_t max_seed = (N + ((int64_t)1 << sd) - 1) >> sd;
+        const int cpn = (int)((max_seed + 31) / 32);
+        seed_scale_kernel<<<grid_of(((int64_t)1 << sd) * cpn * 32, 128), 128, 0, s>>>(
+            tree->xh, tree->xl, N, sd, cpn, pscale);
+        phil_leaf_kernel<<<grid_of(n_leaves * 32, 256), 256, 0, s>>>(pscale, N, n_nodes - n_leaves,
+                                                                     n_leaves, nscale, pscale);
+        for (int dd = tree->depth - 1; dd >= 0; --dd) {
+            const int64_t first = ((int64_t)1 << dd) - 1, cnt = (int64_t)1 << dd;
+            phil_internal_kernel<<<grid_of(cnt, 256), 256, 0, s>>>(first, cnt, nscale);
+        }
+        MBM_CUDA_TRY(cudaGetLastError());
+    }
     const int4 root = make_int4(0, 0, 0, 0);
     MBM_CUDA_TRY(cudaMemcpyAsync(lvl, &root, sizeof(int4), cudaMemcpyHostToDevice, s));
 
@@ -1704,6 +2077,10 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
     p.mc = mcl;
     p.base = basel;
     p.flags = ctx->d_flags;
+    p.nscale = nscale;
+    p.pscale = pscale;
+    p.node_acc3 = node_acc3;
+    p.pt_acc3 = pt_acc3;
 
     const size_t bsm = sizeof(BaseSmem);
     MBM_CUDA_TRY(cudaFuncSetAttribute((const void*)base_group_kernel,
@@ -1728,6 +2105,19 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         }
         base_key_kernel<<<grid_of(n, 256), 256, 0, s>>>(basel, n, N, first_leaf, d, bkey, bval,
                                                         ctr + 12);
+        if (F) {  // exact forces of each leaf triple, a warp each
+            base_forces_kernel<<<grid_of(n * 32, kForceWarps * 32), kForceWarps * 32, 0, s>>>(
+                tree->xh, tree->xl, N, basel, n, pt_acc3);
+            MBM_CUDA_TRY(cudaGetLastError());
+            if (tm.on) {
+                cudaEventRecord(b, s);
+                base_ev.emplace_back(a, b);
+            }
+            if (counting)
+                base_count_kernel<<<grid_of(n * 32, 256), 256, 0, s>>>(N, basel, n, pt_cnt);
+            total_base += n;
+            return MBM_OK;
+        }
         MBM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(sort_tmp, sort_bytes, bkey, bkey2, bval,
                                                      bval2, (int)n, 0, std::max(1, 2 * d), s));
         base_piece_flag_kernel<<<grid_of(n, 256), 256, 0, s>>>(bkey2, n, bflag);
@@ -1771,7 +2161,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         int4* cur = lvl + (size_t)li * cap_lvl + stack[li].done;
         p.next = lvl + (size_t)(li + 1) * cap_lvl;
         MBM_CUDA_TRY(cudaMemsetAsync(ctr, 0, 2 * sizeof(ull), s));  // n_next, n_mc
-        classify_kernel<<<grid_of(take, 256), 256, 0, s>>>(cur, take, p);
+        classify_kernel<F><<<grid_of(take, 256), 256, 0, s>>>(cur, take, p);
         MBM_CUDA_TRY(cudaGetLastError());
         ++n_chunks;
         stack[li].done += take;
@@ -1780,7 +2170,7 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
         const int64_t n_mc = (int64_t)h[1];
         if (n_mc > 0) {
             MBM_CUDA_TRY(cudaMemsetAsync(cand_fail, 0, (size_t)n_mc * sizeof(int), s));
-            mc_probe_kernel<<<grid_of(n_mc * 32, 256), 256, 0, s>>>(mcl, n_mc, cand_fail, p);
+            mc_probe_kernel<F><<<grid_of(n_mc * 32, 256), 256, 0, s>>>(mcl, n_mc, cand_fail, p);
             mc_sizes_kernel<<<grid_of(n_mc, 256), 256, 0, s>>>(mcl, n_mc, N, cand_fail, chunk_off);
             MBM_CUDA_TRY(cudaMemsetAsync(chunk_off + n_mc, 0, sizeof(int64_t), s));
             MBM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(cub_tmp, cub_bytes, chunk_off, chunk_off,
@@ -1794,10 +2184,10 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
                 int64_t c1 = c0 + 1;
                 while (c1 < n_mc && (off[c1 + 1] - off[c0]) * 32 <= cap_est) ++c1;
                 const int64_t chunks = off[c1] - off[c0];
-                mc_kernel<<<grid_of(chunks * 32, 128), 128, 0, s>>>(mcl + c0, 0, c1 - c0,
+                mc_kernel<F><<<grid_of(chunks * 32, 128), 128, 0, s>>>(mcl + c0, 0, c1 - c0,
                                                                     chunk_off + c0, cand_fail + c0,
                                                                     est, p);
-                mc_commit_kernel<<<(unsigned)(c1 - c0), 256, 0, s>>>(
+                mc_commit_kernel<F><<<(unsigned)(c1 - c0), 256, 0, s>>>(
                     mcl + c0, 0, c1 - c0, chunk_off + c0, cand_fail + c0, est, p);
                 MBM_CUDA_TRY(cudaGetLastError());
                 ++n_batches;
@@ -1816,9 +2206,14 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
     n_flushes += n_base > 0;
     tm.mark(3);
     tm.mark(4);
-    finalize_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, tree->depth, n_nodes, n_leaves, tree->perm,
-                                                    pt_acc, node_acc, pt_cnt, node_cnt, phi,
-                                                    cfg.tuple_counts);
+    if (F)
+        finalize3_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, tree->depth, n_nodes, n_leaves,
+                                                         tree->perm, pt_acc3, node_acc3, pt_cnt,
+                                                         node_cnt, phi, cfg.tuple_counts);
+    else
+        finalize_kernel<<<grid_of(N, 256), 256, 0, s>>>(N, tree->depth, n_nodes, n_leaves,
+                                                        tree->perm, pt_acc, node_acc, pt_cnt,
+                                                        node_cnt, phi, cfg.tuple_counts);
     MBM_CUDA_TRY(cudaGetLastError());
     tm.mark(5);
     double base_ms = 0.0;
@@ -1857,10 +2252,22 @@ mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double e
     return MBM_OK;
 }
 
-size_t mbm_tree_solve_bytes(int64_t N, const mbm_config& cfg) {
+mbm_status mbm_tree_potential(mbm_ctx* ctx, const double* X, int64_t N, double eps, double alpha,
+                              bool absolute, const mbm_config& cfg, mbm_tree* tree, double* phi,
+                              mbm_stats* stats, cudaStream_t s) {
+    return tree_solve<false>(ctx, X, N, eps, alpha, absolute, cfg, tree, phi, stats, s);
+}
+
+mbm_status mbm_tree_forces(mbm_ctx* ctx, const double* X, int64_t N, double eps, double alpha,
+                           bool absolute, const mbm_config& cfg, mbm_tree* tree, double* F3,
+                           mbm_stats* stats, cudaStream_t s) {
+    return tree_solve<true>(ctx, X, N, eps, alpha, absolute, cfg, tree, F3, stats, s);
+}
+
+size_t mbm_tree_solve_bytes(int64_t N, const mbm_config& cfg, bool forces) {
     if (N < 3 || cfg.leaf_size < 2) return 0;
     const int depth = tree_depth(N, cfg.leaf_size);
     const int64_t n_nodes = ((int64_t)2 << depth) - 1;
-    const TravPlan plan = trav_plan(N, depth, cfg);
+    const TravPlan plan = trav_plan(N, depth, cfg, forces);
     return carve_size(tree_parts(N, n_nodes)) + carve_size(plan.parts);
 }
