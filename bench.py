@@ -194,14 +194,28 @@ def bench_fp64(api, inputs, torch, dev):
 
 
 def bench_tree(api, inputs, torch, dev, r64, np, workload="gmm4_n65536", eps_list=(1e-2, 1e-1),
-               warm=True, n_sample=256, progress=False):
+               warm=True, n_sample=256, progress=False, exact_file=None):
     """Tree solves (relative eps, alpha 0.05) timed end to end from device-resident X;
-    accuracy on n_sample seeded particles against the exact sampled sum."""
+    accuracy on n_sample seeded particles against the exact sampled sum (read
+    from exact_file when it holds this workload's sample, else computed and,
+    with exact_file given, saved there)."""
     X = inputs.workload(workload)
     n = len(X)
     Xd = torch.from_numpy(X).to(dev)
     idx = inputs.sample_indices(n, n_sample, 11)
-    exact = api.potential_sampled(Xd, idx).cpu().numpy()
+    exact = None
+    if exact_file and os.path.exists(exact_file):
+        saved = np.load(exact_file)
+        if saved["n"] == n and np.array_equal(saved["idx"], idx):
+            exact = saved["exact"]
+    if exact is None:
+        t0 = time.perf_counter()
+        exact = api.potential_sampled(Xd, idx).cpu().numpy()
+        if progress:
+            print(json.dumps({"progress": workload, "sampled_exact_s": time.perf_counter() - t0}),
+                  flush=True)
+        if exact_file:
+            np.savez(exact_file, n=n, idx=idx, exact=exact)
     out = {"workload": workload, "n": n, "alpha": 0.05, "sampled_particles": len(idx)}
     fp64_pps = n * r64 / triples(n)                       # plain FP64 exhaustive particles/s
     fp64_pps_config3 = N_CONFIG3 * r64 / triples(N_CONFIG3)
@@ -209,10 +223,14 @@ def bench_tree(api, inputs, torch, dev, r64, np, workload="gmm4_n65536", eps_lis
         if warm:
             api.potential(Xd, eps=eps, alpha=0.05, mode="tree")  # warm-up
         torch.cuda.synchronize()
+        sampler = ClockSampler(dev.index or 0) if progress else None
+        if sampler:
+            sampler.start()
         t0 = time.perf_counter()
         phi, st = api.potential(Xd, eps=eps, alpha=0.05, mode="tree", stats=True)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        clocks = sampler.stop() if sampler else None
         rel = np.abs(phi.cpu().numpy()[idx] - exact) / np.abs(exact)
         out[f"eps_{eps:g}"] = {
             "particles_per_s": n / dt, "s": dt, "within_eps": float(np.mean(rel <= eps)),
@@ -221,6 +239,8 @@ def bench_tree(api, inputs, torch, dev, r64, np, workload="gmm4_n65536", eps_lis
                          ("ms_build", "ms_traverse", "ms_base", "ms_finalize")},
             "det_prunes": st["det_prunes"], "mc_prunes": st["mc_prunes"],
             "base_triples": st["base_triples"], "mc_samples": st["mc_samples"]}
+        if clocks:
+            out[f"eps_{eps:g}"]["clocks"] = clocks
         if progress:
             print(json.dumps({"progress": workload, f"eps_{eps:g}": out[f"eps_{eps:g}"]}),
                   flush=True)
@@ -296,6 +316,137 @@ def bench_serving(api, inputs, np, duration=6.0, rate=200.0):
             "mix": "70% tree Phi (eps 1e-2, alpha 0.05, resident systems), 30% FP32 forces"}
 
 
+def _config5_system(n, q):
+    """One system of the serving workload: uniform at density 1 (d_min 0.5) for
+    even q, else the Gaussian-mixture generator of the N = 2^20 set scaled to
+    n (components of 16 384 points at the same component density)."""
+    from paper_1105_2769_gb300 import inputs
+    if q % 2 == 0:
+        return inputs.uniform_cube(n, n ** (1 / 3), 0.5, 700 + q)
+    comps = max(1, n // 16384)
+    return inputs.gaussian_mixture(n, comps, 100.0 * (comps / 64) ** (1 / 3), 0.5, 3.0, 0.05,
+                                   700 + q)
+
+
+def run_serving_only(args):
+    """The serving workload as specified: Poisson arrivals at 200 req/s for 60 s,
+    N log-uniform in [1 024, 262 144] (a pool of seeded systems, half uniform,
+    half mixture), 70 % Phi / 30 % forces, both by the tree method at eps = 1e-2,
+    alpha = 0.05, systems kept resident, 120 GB budget, 8 slots. After the
+    offered window the server drains for at most `drain` s; requests still
+    queued then are reported, not waited for."""
+    import numpy as np
+    import torch  # noqa: F401  (CUDA context for the library)
+
+    from paper_1105_2769_gb300 import api
+    rate, duration, drain = args.serve_rate, args.serve_seconds, args.serve_drain
+    rng = np.random.default_rng(5)
+    pool_n = [int(np.exp(rng.uniform(np.log(1024), np.log(262144)))) for _ in range(args.serve_pool)]
+    t0 = time.perf_counter()
+    pool = [_config5_system(n, q) for q, n in enumerate(pool_n)]
+    gen_s = time.perf_counter() - t0
+    srv = api.Server(0, hbm_budget_bytes=120 << 30, slots=8)
+    n_req = int(duration * rate)
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    is_phi = rng.uniform(size=n_req) < 0.7
+    picks = rng.integers(0, len(pool), size=n_req)
+    tickets = []
+    t_start = time.perf_counter()
+    t_next = t_start
+    for q in range(n_req):
+        t_next += gaps[q]
+        while time.perf_counter() < t_next:
+            time.sleep(0.0002)
+        X = pool[picks[q]]
+        kind = "potential" if is_phi[q] else "forces"
+        try:
+            tickets.append((q, srv.submit(X, kind=kind, mode="tree", eps=1e-2, alpha=0.05,
+                                          system_id=int(picks[q]) + 1)))
+        except Exception:  # rejected by the budget
+            tickets.append((q, None))
+    t_offer = time.perf_counter() - t_start
+    lat, comp, parts_done, done_kinds, iv = [], [], 0, [], []
+    deadline = t_start + duration + drain
+    pending = 0
+    for q, t in tickets:
+        if t is None:
+            continue
+        left = deadline - time.perf_counter()
+        st, res, _ = srv.poll(t, timeout_us=max(0, int(left * 1e6)))
+        if res is None:
+            pending += 1
+            continue
+        lat.append(res["latency_ms"])
+        comp.append(res["compute_ms"])
+        parts_done += len(pool[picks[q]])
+        done_kinds.append(bool(is_phi[q]))
+        iv.append((res["dev_start_ns"], res["dev_end_ns"]))
+    wall = time.perf_counter() - t_start
+    stats = srv.stats()
+    # device concurrency: the largest number of requests whose device intervals overlap
+    ev = sorted([(a, 1) for a, b in iv if b > a] + [(b, -1) for a, b in iv if b > a])
+    cur = peak = 0
+    for _, d in ev:
+        cur += d
+        peak = max(peak, cur)
+    srv.close()
+    rep = {"report": "serving", "offered_req_per_s": rate, "offered_s": t_offer,
+           "requests_offered": n_req, "drain_s": drain, "completed": len(lat),
+           "not_completed_at_deadline": pending,
+           "rejected": stats["rejected"], "admitted": stats["admitted"],
+           "served_req_per_s": len(lat) / wall, "particles_per_s": parts_done / wall,
+           "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+           "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+           "compute_ms_p50": float(np.percentile(comp, 50)) if comp else None,
+           "completed_phi": int(sum(done_kinds)), "completed_forces": len(done_kinds) - int(sum(done_kinds)),
+           "max_requests_overlapping_on_device": peak, "slots": 8, "budget_gb": 120,
+           "pool": {"systems": len(pool), "n_min": min(pool_n), "n_max": max(pool_n),
+                    "generation_s": gen_s},
+           "mix": "70% Phi / 30% forces, tree eps 1e-2 alpha 0.05, resident systems"}
+    print(json.dumps(rep))
+    return 0
+
+
+def run_forces_only(args):
+    """Forces of the N = 65 536 force workload (uniform [0,32]^3, d_min 0.5,
+    seed 4): the exhaustive FP32-bulk adjoint timed once, and the tree forces
+    at eps = 1e-2 (alpha 0.05) of the same set, with accuracy on sampled
+    particles against the exhaustive result."""
+    import numpy as np
+    import torch
+
+    from paper_1105_2769_gb300 import api, inputs
+    dev = torch.device("cuda", 0)
+    n = args.forces_n
+    X = inputs.workload("forces_n65536") if n == 65536 else \
+        inputs.uniform_cube(n, 32.0 * (n / 65536) ** (1 / 3), 0.5, 4)
+    Xd = torch.from_numpy(X).to(dev)
+    rep = {"report": "forces", "n": n, "workload": "uniform [0,32]^3 density 2, d_min 0.5, seed 4"}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    F = api.forces(Xd, mode="fp32")
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rep["exhaustive_fp32"] = {"s": dt, "triples_per_s": triples(n) / dt}
+    print(json.dumps({"progress": rep}), flush=True)
+    Fe = F.cpu().numpy()
+    for eps in (1e-2,):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Ft, st = api.forces(Xd, eps=eps, alpha=0.05, mode="tree", stats=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        d = np.abs(Ft.cpu().numpy() - Fe).max(axis=1) / np.linalg.norm(Fe, axis=1)
+        rep[f"tree_eps_{eps:g}"] = {
+            "s": dt, "particles_per_s": n / dt, "speedup_vs_exhaustive_fp32": rep["exhaustive_fp32"]["s"] / dt,
+            "phase_ms": {k: round(st[k], 2) for k in ("ms_build", "ms_traverse", "ms_base")},
+            "det_prunes": st["det_prunes"], "mc_prunes": st["mc_prunes"],
+            "base_triples": st["base_triples"],
+            "max_dev_over_abs_force": float(d.max()), "median_dev_over_abs_force": float(np.median(d))}
+    print(json.dumps(rep))
+    return 0
+
+
 def run_paper_shape(args):
     """The paper's experiment shapes (Sec. 6) on this GPU: uniform cube, unit
     ball and thin shell ("annulus"), tree solves at eps 1e-1/1e-2/1e-3 and
@@ -345,7 +496,8 @@ def run_tree_only(args):
     fp64 = bench_fp64(api, inputs, torch, dev)
     eps_list = tuple(float(e) for e in args.tree_eps.split(","))
     rep = bench_tree(api, inputs, torch, dev, fp64["triples_per_s"], np, workload=args.tree_only,
-                     eps_list=eps_list, warm=False, n_sample=args.tree_sample, progress=True)
+                     eps_list=eps_list, warm=False, n_sample=args.tree_sample, progress=True,
+                     exact_file=args.tree_exact_file)
     rep["fp64_exhaustive"] = fp64
     print(json.dumps({"report": "tree", **rep}))
     return 0
@@ -364,8 +516,19 @@ def main():
                          "solve per eps without warm-up, and print their JSON report")
     ap.add_argument("--tree-eps", default="1e-2,1e-1")
     ap.add_argument("--tree-sample", type=int, default=256)
+    ap.add_argument("--tree-exact-file", default=None,
+                    help="npz cache of the sampled exact sums used by --tree-only")
     ap.add_argument("--paper-shape", action="store_true",
                     help="tree vs FP64 exhaustive on the paper's uniform/ball/shell shapes")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="the serving workload as specified (60 s Poisson stream, N up to 2^18)")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-drain", type=float, default=60.0)
+    ap.add_argument("--serve-pool", type=int, default=32)
+    ap.add_argument("--forces-only", action="store_true",
+                    help="exhaustive and tree forces of the N = 65 536 force workload")
+    ap.add_argument("--forces-n", type=int, default=65536)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -373,6 +536,10 @@ def main():
         return run_tree_only(args)
     if args.paper_shape:
         return run_paper_shape(args)
+    if args.serving_only:
+        return run_serving_only(args)
+    if args.forces_only:
+        return run_forces_only(args)
 
     import numpy as np
     import torch

@@ -252,8 +252,11 @@ mbm_status mbm_potential_vjp(mbm_ctx* ctx, const double* X_dev, int64_t N, const
  * No device memory is allocated or freed: scratch is a fixed 2 MiB + 256 B
  * file-scope device array that every GPU loading the library holds until
  * exit. The first call on a device resolves that array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture. Every call shares the one array, so calls whose work
+ * (cudaGetSymbolAddress) and caches it for the rest of the process; make
+ * that first call before any stream capture. The cached address belongs to
+ * the device's primary context: after cudaDeviceReset (or with another
+ * context current) it is stale, so such callers must not use this entry
+ * point again in the same process. Every call shares the one array, so calls whose work
  * overlaps on the GPU (different streams, or concurrent host threads) race;
  * serialise them. No input validation on the device: non-finite or
  * coincident points give non-finite results rather than MBM_EINVAL.

@@ -11,7 +11,10 @@
 //
 // Host code cannot use the array's name as a device address (on the host it
 // names a stand-in object), so the first call on each device resolves the
-// address with cudaGetSymbolAddress, with that device current, and caches it.
+// address with cudaGetSymbolAddress, with that device current, and caches it
+// for the process. The cache assumes the device's primary context lives as
+// long as the process: a caller that resets the device must not call this
+// entry point again (include/mbm.h says so).
 #include <mutex>
 
 #include "mbm_internal.h"

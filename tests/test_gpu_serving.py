@@ -1,7 +1,8 @@
 """Serving engine (step a11): continuous batching on one GPU.
 
-  * each result of a mixed stream (exhaustive and tree potentials, forces,
-    uneven N, resident systems) equals the same request solved alone through
+  * each result of a mixed stream (exhaustive and tree potentials, exhaustive
+    and tree forces, uneven N, resident systems) equals the same request
+    solved alone through
     the direct API: the arithmetic of a request does not depend on what runs
     beside it (Philox draws are keyed by particle and node ids), so only the
     order of FP64 atomic additions differs: |difference| <= 1e-10 max|result|;
@@ -23,7 +24,7 @@ pytestmark = pytest.mark.gpu
 def _alone(X, kind, mode, eps, alpha):
     Xd = torch.from_numpy(X).cuda()
     if kind == "forces":
-        return api.forces(Xd, mode=mode).cpu().numpy()
+        return api.forces(Xd, mode=mode, eps=eps, alpha=alpha).cpu().numpy()
     return api.potential(Xd, eps=eps, alpha=alpha, mode=mode).cpu().numpy()
 
 
@@ -42,8 +43,11 @@ def _mix(seed):
         elif r == 1:
             reqs.append(dict(X=X, kind="potential", mode="tree", eps=1e-2, alpha=0.05,
                              system_id=q if q % 4 == 1 else 0))
-        else:
+        elif q % 2:
             reqs.append(dict(X=X, kind="forces", mode="fp32", eps=0.0, alpha=0.0))
+        else:  # tree forces, resident for some
+            reqs.append(dict(X=X, kind="forces", mode="tree", eps=1e-2, alpha=0.05,
+                             system_id=q if q % 4 == 0 else 0))
     return reqs
 
 

@@ -5,9 +5,10 @@ own every device byte through their own pool, loops that cannot afford the
 synchronisation of an allocation, plugins in processes that forbid foreign
 allocations) use this entry point; its scratch is a fixed device array.
 The test calls it through the C ABI twice in a row, on two sizes, and checks
-each result against the regular FP32 entry point with the FP32 bar used by
-the other exhaustive tests (error <= 3e-6 of sum_t |phi_t|). It lives in a
-file collected last so that a failure here cannot hide another test's."""
+each result against the regular FP32 entry point and against the FP64 oracle
+with the FP32 bar used by the other exhaustive tests (error <= 3e-6 of
+sum_t |phi_t|). It lives in a file collected last so that a failure here
+cannot hide another test's."""
 import ctypes
 
 import numpy as np
@@ -35,11 +36,12 @@ def test_noalloc_matches_regular_entry_point(n, seed):
     X = inputs.uniform_cube(n, 4.0, 0.05, seed)
     Xd = torch.from_numpy(X).cuda()
     ref = api.potential(Xd, mode="fp32").cpu().numpy()
-    _, abs_sum = oracle.phi(X, with_abs=True)
+    exact, abs_sum = oracle.phi(X, with_abs=True)
     for _ in range(2):  # two calls in a row share the static scratch
         out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
         got = _noalloc(Xd, out)
         assert np.all(np.abs(got - ref) <= 3e-6 * abs_sum)
+        assert np.all(np.abs(got - exact) <= 3e-6 * abs_sum)
 
 
 def test_noalloc_rejects_oversize():
