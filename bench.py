@@ -462,7 +462,7 @@ def run_paper_shape(args):
             "shell": lambda n: inputs.spherical_shell(n, 0.95, 1.0, 1e-3, 43)}
     rows = []
     for name, gen in sets.items():
-        for n in (2000, 10000):
+        for n in args.paper_n:
             X = gen(n)
             Xd = torch.from_numpy(X).to(dev)
             api.potential(Xd, mode="fp64")
@@ -481,7 +481,9 @@ def run_paper_shape(args):
                     rows.append({"set": name, "n": n, "eps": eps, "alpha": alpha,
                                  "tree_s": dt, "fp64_exhaustive_s": t_ex,
                                  "speedup": t_ex / dt, "within_eps": float(np.mean(rel <= eps)),
-                                 "mean_rel_err": float(rel.mean()), "max_rel_err": float(rel.max())})
+                                 "mean_rel_err": float(rel.mean()),
+                                 "var_rel_err": float(rel.var()),
+                                 "max_rel_err": float(rel.max())})
                     print(json.dumps(rows[-1]), flush=True)
     print(json.dumps({"report": "paper_shape", "rows": len(rows)}))
     return 0
@@ -520,6 +522,7 @@ def main():
                     help="npz cache of the sampled exact sums used by --tree-only")
     ap.add_argument("--paper-shape", action="store_true",
                     help="tree vs FP64 exhaustive on the paper's uniform/ball/shell shapes")
+    ap.add_argument("--paper-n", type=int, nargs="+", default=list(range(1000, 10001, 1000)))
     ap.add_argument("--serving-only", action="store_true",
                     help="the serving workload as specified (60 s Poisson stream, N up to 2^18)")
     ap.add_argument("--serve-rate", type=float, default=200.0)

@@ -33,8 +33,6 @@
 // and Phi^l is fixed before the traversal, so this order makes the same
 // decisions as a depth-first recursion. Monte Carlo samples are FP32 phi
 // values, so a stop test on the edge may rarely differ from an FP64 sample.
-#include <cub/cub.cuh>
-
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -43,6 +41,7 @@
 #include <vector>
 
 #include "mbm_tree_api.h"
+#include "sort_scan.h"
 #include "tile_fp32.cuh"
 
 struct mbm_tree {
@@ -139,7 +138,7 @@ __global__ void bbox_final_kernel(const double* part, int nb, double* box) {
 }
 
 __global__ void morton_kernel(const double* __restrict__ X, int64_t N, const double* box,
-                              uint64_t* keys, int* idx, int* flags) {
+                              unsigned long long* keys, int* idx, int* flags) {
     const double l0 = box[0], l1 = box[1], l2 = box[2];
     double ext = __dsub_rn(box[3], l0);
     if (__dsub_rn(box[4], l1) > ext) ext = __dsub_rn(box[4], l1);
@@ -1661,7 +1660,7 @@ std::vector<size_t> tree_parts(int64_t N, int64_t n_nodes) {
 struct TravPlan {
     int64_t B = 0, cap_lvl = 0, cap_mc = 0, cap_base = 0, cap_est = 0;
     int max_levels = 0;
-    size_t cub_bytes = 0, sort_bytes = 0;
+    size_t scan_tmp_bytes = 0, sort_bytes = 0;
     std::vector<size_t> parts;
 };
 
@@ -1690,16 +1689,11 @@ TravPlan trav_plan(int64_t N, int depth, const mbm_config& cfg, bool forces) {
     // to 32-point chunks) never exceed N + 96, so every batch holds at least one
     q.cap_est = 3 * N + 64 * 1024;
     if (cfg.est_cap > 0) q.cap_est = std::max<int64_t>(N + 128, cfg.est_cap);
-    cub::DeviceScan::ExclusiveSum(nullptr, q.cub_bytes, (int64_t*)nullptr, (int64_t*)nullptr,
-                                  (int)(q.cap_mc + 1));
+    q.scan_tmp_bytes = mbm_scan_temp_bytes_i64(q.cap_mc + 1);
     // Base-case grouping: radix sort of (y, z) keys over 2 * depth bits and a
     // scan of piece flags share one temporary buffer.
-    size_t scan_bytes = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, q.sort_bytes, (ull*)nullptr, (ull*)nullptr,
-                                    (int*)nullptr, (int*)nullptr, (int)q.cap_base, 0,
-                                    std::max(1, 2 * depth));
-    cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, (int*)nullptr, (int*)nullptr,
-                                  (int)q.cap_base);
+    q.sort_bytes = mbm_sort_temp_bytes(q.cap_base);
+    const size_t scan_bytes = mbm_scan_temp_bytes_i32(q.cap_base);
     q.sort_bytes = std::max(q.sort_bytes, scan_bytes);
     const size_t cb = (size_t)q.cap_base;
     q.parts = {
@@ -1708,7 +1702,7 @@ TravPlan trav_plan(int64_t N, int depth, const mbm_config& cfg, bool forces) {
         (size_t)q.max_levels * q.cap_lvl * 16,                             // level buffers
         (size_t)q.cap_mc * 16, cb * 16,                                    // mc, base
         (size_t)(q.cap_mc + 2) * 8, (size_t)q.cap_mc * 4,                  // chunk_off, fail
-        (size_t)q.cap_est * (forces ? 24 : 8), 256, q.cub_bytes,           // est, counters
+        (size_t)q.cap_est * (forces ? 24 : 8), 256, q.scan_tmp_bytes,      // est, counters
         (size_t)(m_limit + 1) * 8,                                         // 1/m table
         cb * 8, cb * 8, cb * 4, cb * 4,                                    // base keys, x
         (cb + 1) * 4, (cb + 1) * 4, (cb + 1) * 4, 64, q.sort_bytes,        // flag pos heads
@@ -1768,15 +1762,13 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
 
     // Temporary scratch: box partials, keys/indices (double-buffered), CUB temp, seed sums.
     const int nb = 256;
-    size_t cub_bytes = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, cub_bytes, (uint64_t*)nullptr, (uint64_t*)nullptr,
-                                    (int*)nullptr, (int*)nullptr, (int)N, 0, 63, s);
+    const size_t sort_tmp_bytes = mbm_sort_temp_bytes(N);
     const int sd = std::max(0, depth - cfg.seed_levels);
     const int64_t max_seed = (N + ((int64_t)1 << sd) - 1) >> sd;  // ceil(N / 2^sd)
     const int chunks = (int)((max_seed + kTile - 1) / kTile);
     const std::vector<int4> cmb = chunk_combos(chunks);
     const std::vector<size_t> sparts = {(size_t)nb * 48, 64, (size_t)N * 8, (size_t)N * 8,
-                                        (size_t)N * 4, (size_t)N * 4, cub_bytes, (size_t)N * 8,
+                                        (size_t)N * 4, (size_t)N * 4, sort_tmp_bytes, (size_t)N * 8,
                                         cmb.size() * 16};
     st = mbm_scratch_reserve(ctx, carve_size(sparts));
     if (st != MBM_OK) {
@@ -1786,11 +1778,11 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
     Carve sc{static_cast<char*>(ctx->scratch)};
     double* part = sc.take<double>(nb * 6);
     double* box = sc.take<double>(8);
-    uint64_t* k0 = sc.take<uint64_t>(N);
-    uint64_t* k1 = sc.take<uint64_t>(N);
+    ull* k0 = sc.take<ull>(N);
+    ull* k1 = sc.take<ull>(N);
     int* i0 = sc.take<int>(N);
     int* i1 = sc.take<int>(N);
-    void* cub_tmp = sc.take<char>(cub_bytes);
+    void* sort_tmp = sc.take<char>(sort_tmp_bytes);
     double* seed = sc.take<double>(N);
     int4* combos = sc.take<int4>(cmb.size());
 
@@ -1807,7 +1799,7 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
     bbox_final_kernel<<<1, 32, 0, s>>>(part, nb, box);
     morton_kernel<<<grid_of(N, 256), 256, 0, s>>>(X, N, box, k0, i0, ctx->d_flags);
     TRY_LAUNCH();
-    e = cub::DeviceRadixSort::SortPairs(cub_tmp, cub_bytes, k0, k1, i0, i1, (int)N, 0, 63, s);
+    e = mbm_sort_pairs_u64(k0, k1, i0, i1, N, 0, 63, sort_tmp, s);
     if (e != cudaSuccess) {
         mbm_tree_free(t);
         return mbm_cuda_fail(e, "radix sort");
@@ -1966,7 +1958,7 @@ static mbm_status tree_solve(mbm_ctx* ctx, const double* X, int64_t N, double ep
     const int64_t B = plan.B, cap_lvl = plan.cap_lvl, cap_mc = plan.cap_mc;
     const int64_t cap_base = plan.cap_base, cap_est = plan.cap_est;
     const int max_levels = plan.max_levels;
-    size_t cub_bytes = plan.cub_bytes, sort_bytes = plan.sort_bytes;
+    size_t scan_tmp_bytes = plan.scan_tmp_bytes, sort_bytes = plan.sort_bytes;
     const int d = tree->depth;
     const int64_t first_leaf = n_nodes - n_leaves;
     const double z = z_two_sided(alpha);
@@ -1984,7 +1976,7 @@ static mbm_status tree_solve(mbm_ctx* ctx, const double* X, int64_t N, double ep
     int* cand_fail = sc.take<int>(cap_mc);
     double* est = sc.take<double>(cap_est * (F ? 3 : 1));
     ull* ctr = sc.take<ull>(32);  // 0 n_next, 1 n_mc, 2 n_base, 3.. statistics
-    void* cub_tmp = sc.take<char>(cub_bytes);
+    void* scan_tmp = sc.take<char>(scan_tmp_bytes);
     double* rcp = sc.take<double>(cfg.m_limit + 1);
     ull* bkey = sc.take<ull>(cap_base);
     ull* bkey2 = sc.take<ull>(cap_base);
@@ -2118,10 +2110,10 @@ static mbm_status tree_solve(mbm_ctx* ctx, const double* X, int64_t N, double ep
             total_base += n;
             return MBM_OK;
         }
-        MBM_CUDA_TRY(cub::DeviceRadixSort::SortPairs(sort_tmp, sort_bytes, bkey, bkey2, bval,
-                                                     bval2, (int)n, 0, std::max(1, 2 * d), s));
+        MBM_CUDA_TRY(mbm_sort_pairs_u64(bkey, bkey2, bval, bval2, n, 0, std::max(1, 2 * d),
+                                        sort_tmp, s));
         base_piece_flag_kernel<<<grid_of(n, 256), 256, 0, s>>>(bkey2, n, bflag);
-        MBM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(sort_tmp, sort_bytes, bflag, bpos, (int)n, s));
+        MBM_CUDA_TRY(mbm_exclusive_scan_i32(bflag, bpos, n, sort_tmp, s));
         base_piece_heads_kernel<<<grid_of(n, 256), 256, 0, s>>>(bflag, bpos, n, bheads, bmeta);
         MBM_CUDA_TRY(cudaMemsetAsync(bmeta + 1, 0, sizeof(int), s));
         base_group_kernel<<<base_grid, kBaseWarps * 32, bsm, s>>>(
@@ -2173,8 +2165,7 @@ static mbm_status tree_solve(mbm_ctx* ctx, const double* X, int64_t N, double ep
             mc_probe_kernel<F><<<grid_of(n_mc * 32, 256), 256, 0, s>>>(mcl, n_mc, cand_fail, p);
             mc_sizes_kernel<<<grid_of(n_mc, 256), 256, 0, s>>>(mcl, n_mc, N, cand_fail, chunk_off);
             MBM_CUDA_TRY(cudaMemsetAsync(chunk_off + n_mc, 0, sizeof(int64_t), s));
-            MBM_CUDA_TRY(cub::DeviceScan::ExclusiveSum(cub_tmp, cub_bytes, chunk_off, chunk_off,
-                                                       (int)(n_mc + 1), s));
+            MBM_CUDA_TRY(mbm_exclusive_scan_i64(chunk_off, chunk_off, n_mc + 1, scan_tmp, s));
             off.resize(n_mc + 1);
             MBM_CUDA_TRY(cudaMemcpyAsync(off.data(), chunk_off, (n_mc + 1) * sizeof(int64_t),
                                          cudaMemcpyDeviceToHost, s));

@@ -252,3 +252,46 @@ def test_library_defaults_against_the_oracle(eps):
     assert (np.abs(phi - ref) <= FP32_BAR * ab).mean() >= 0.99
     slack = 3.0 * np.sqrt(alpha * (1 - alpha) / len(X))
     assert (np.abs(phi - ex) <= eps * np.abs(ex)).mean() >= 1 - alpha - slack
+
+
+@pytest.mark.parametrize("shape", ["ball", "shell"])
+def test_paper_shapes_against_the_oracle(shape):
+    """The paper's ball and thin-shell ("annulus") sets (Sec. 6) at N = 1 500:
+    deterministic prunes equal to the restatement's and results within the
+    FP32 bar of it (alpha = 0), Monte Carlo prune counts within 2 % and >= 99 %
+    of particles equal (alpha = 0.1, the paper's Monte Carlo setting), and the
+    guarantees against the exact sum."""
+    n = 1500
+    X = inputs.unit_ball(n, 1e-3, 42) if shape == "ball" else \
+        inputs.spherical_shell(n, 0.95, 1.0, 1e-3, 43)
+    ex, ab = oracle.phi(X, with_abs=True)
+    for eps, alpha in ((0.1, 0.0), (0.01, 0.0), (0.1, 0.1)):
+        phi, cnt, st = _gpu_tree(X, eps, alpha, zeta=4.0)
+        ref, _, rst = otree.tree_potential(X, eps=eps, alpha=alpha, zeta=4.0, with_counts=True)
+        print(f"{shape} eps={eps} alpha={alpha}: det {st['det_prunes']}/{rst['det_prunes']} "
+              f"mc {st['mc_prunes']}/{rst['mc_prunes']}")
+        assert np.all(cnt == comb(n - 1, 2))
+        assert st["det_prunes"] == rst["det_prunes"]
+        within = np.abs(phi - ex) <= eps * np.abs(ex) + FP32_BAR * ab
+        if alpha == 0.0:
+            assert np.all(np.abs(phi - ref) <= FP32_BAR * ab)
+            assert within.all()
+        else:
+            assert abs(st["mc_prunes"] - rst["mc_prunes"]) <= max(2, 0.02 * rst["mc_prunes"])
+            assert (np.abs(phi - ref) <= FP32_BAR * ab).mean() >= 0.99
+            assert within.mean() >= 1 - alpha - 3.0 * np.sqrt(alpha * (1 - alpha) / n)
+
+
+def test_tree_layout_large_matches_definition():
+    """N = 20 000 (several sort tiles per pass): the Morton permutation (ties by
+    index), node boxes and centres equal the oracle's definition exactly, so
+    the device radix sort is stable and complete across tiles."""
+    X = inputs.uniform_cube(20000, 20.0, 0.05, 33)
+    X[:50] = X[50:100] + 2e-7  # near-duplicates: equal Morton keys, ordered by index
+    t = api.Tree(torch.from_numpy(np.ascontiguousarray(X)).cuda())
+    got = t.export()
+    ref = otree.tree_layout(X, 32)
+    assert np.array_equal(got["perm"], ref["perm"])
+    assert np.array_equal(got["lo"], ref["lo"]) and np.array_equal(got["hi"], ref["hi"])
+    np.testing.assert_allclose(got["cen"], ref["cen"], rtol=1e-13, atol=1e-12)
+    t.close()

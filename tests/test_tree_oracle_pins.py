@@ -144,7 +144,8 @@ _TREE_MUTANTS = {
     "Fig. 4 case (b) count": ("(n[0] - 1.0) * n[2];     /* (b) */", "n[0] * n[2];     /* (b) */"),
     "Fig. 4 case (c) count": ("n[0] * (n[1] - 1.0);     /* (c) */", "n[0] * n[1];     /* (c) */"),
     "Fig. 4 case (d) slot": ("if (slot == 0) return n[1] * n[2];", "if (slot == 0) return n[0] * n[2];"),
-    "budget without T^root": ("+ S->tau) / S->troot;", "+ S->tau);"),
+    "budget without T^root": ("(lb > 0.0 ? lb : 0.0) + S->tau) / S->troot;",
+                              "(lb > 0.0 ? lb : 0.0) + S->tau);"),
 }
 
 
