@@ -56,6 +56,7 @@ def lib():
             L.oracle_at_phi.restype = ctypes.c_double
             L.oracle_at_phi.argtypes = [dp, dp, dp]
             L.oracle_phi.argtypes = [dp, i64, ip, i64, dp, dp, ctypes.c_int]
+            L.oracle_phi_parts.argtypes = [dp, i64, ip, i64, dp, ctypes.c_int]
             L.oracle_energy.argtypes = [dp, i64, dp, ctypes.c_int]
             L.oracle_grad.argtypes = [dp, i64, ip, i64, dp, dp, ctypes.c_int]
             L.oracle_vjp.argtypes = [dp, i64, dp, ip, i64, dp, dp, ctypes.c_int]
@@ -105,6 +106,19 @@ def phi(X, idx=None, with_abs=False, nthreads=0):
     if rc != 0:
         raise RuntimeError(f"oracle_phi failed ({rc})")
     return (out, ab) if with_abs else out
+
+
+def phi_parts(X, idx=None, nthreads=0):
+    """Sum over the terms of Phi(x_i) of (1 + 3|cos cos cos|)/(r r r)^3: the
+    magnitudes of each term's two parts, the scale of its rounding error."""
+    X = _points(X)
+    n = len(X)
+    idx = np.arange(n, dtype=np.int64) if idx is None else np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(len(idx))
+    rc = lib().oracle_phi_parts(_dp(X), n, _ip(idx), len(idx), _dp(out), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_phi_parts failed ({rc})")
+    return out
 
 
 def energy(X, nthreads=0) -> float:

@@ -106,6 +106,39 @@ int oracle_phi(const double* X, int64_t N, const int64_t* idx, int64_t n_idx,
     return 0;
 }
 
+/* Sum over the terms of Phi(x_i) of the magnitudes of their two parts,
+ * (1 + 3 |cos_i cos_j cos_k|) / (r_ij^3 r_ik^3 r_jk^3): the scale of the
+ * rounding error of evaluating each term, which |phi| understates where
+ * 1 + 3 cos cos cos cancels inside a term. */
+int oracle_phi_parts(const double* X, int64_t N, const int64_t* idx, int64_t n_idx, double* out,
+                     int nthreads) {
+    if (N < 0 || n_idx < 0) return -1;
+    int nt = nthreads_or_default(nthreads);
+    int64_t q;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (q = 0; q < n_idx; ++q) {
+        int64_t i = idx[q];
+        nsum_t acc = {0.0, 0.0};
+        const double* xi = X + 3 * i;
+        for (int64_t j = 0; j < N; ++j) {
+            if (j == i) continue;
+            for (int64_t k = j + 1; k < N; ++k) {
+                if (k == i) continue;
+                double u[3], v[3], w[3];
+                sub3(X + 3 * j, xi, u); sub3(X + 3 * k, xi, v); sub3(X + 3 * k, X + 3 * j, w);
+                double ru = sqrt(dot3(u, u)), rv = sqrt(dot3(v, v)), rw = sqrt(dot3(w, w));
+                double ci = dot3(u, v) / (ru * rv);
+                double cj = -dot3(u, w) / (ru * rw);
+                double ck = dot3(v, w) / (rv * rw);
+                double D = ru * ru * ru * rv * rv * rv * rw * rw * rw;
+                nsum_add(&acc, (1.0 + 3.0 * fabs(ci * cj * ck)) / D);
+            }
+        }
+        out[q] = nsum_get(&acc);
+    }
+    return 0;
+}
+
 /* Total three-body energy E = sum over unordered triples a < b < c. */
 int oracle_energy(const double* X, int64_t N, double* out, int nthreads) {
     if (N < 0) return -1;

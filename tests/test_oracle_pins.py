@@ -263,3 +263,21 @@ def test_pins_reject_planted_mistakes(tmp_path, name):
         assert _pins_hold(at_phi, phi)
     else:
         assert not _pins_hold(at_phi, phi), f"the pins did not catch: {name}"
+
+
+def test_phi_parts_closed_forms(oracle_lib):
+    """The rounding scale sum_t (1 + 3|cos cos cos|)/(r r r)^3 of each term:
+    equal to |phi| where the cosine product is >= 0 (equilateral: 1/8; right
+    angle: 0), larger where it is negative: collinear, cosine product -1,
+    (1 + 3)/(1 * 8 * 1) = 0.5 (|phi| = 0.25); 120-degree isosceles, product
+    -0.375, (1 + 1.125)/3^1.5 (|phi| = 0.125/3^1.5)."""
+    for name, pts, expected, _why in _read_fixture("closed_forms.txt"):
+        P = np.array([[float(v) for v in p.split()] for p in pts.split(";")])
+        parts = oracle_lib.phi_parts(P)
+        assert np.all(parts >= np.abs(float(expected)) * (1 - 1e-13)), name
+        if name.startswith(("equilateral", "right_angle")):
+            np.testing.assert_allclose(parts, abs(float(expected)), rtol=1e-13, err_msg=name)
+    col = np.array([[0, 0, 0], [1, 0, 0], [2, 0, 0]], dtype=np.float64)
+    np.testing.assert_allclose(oracle_lib.phi_parts(col), 0.5, rtol=1e-13)
+    iso = np.array([[0, 0, 0], [1, 0, 0], [-0.5, np.sqrt(3) / 2, 0]])
+    np.testing.assert_allclose(oracle_lib.phi_parts(iso)[0], 2.125 / 3 ** 1.5, rtol=1e-12)
