@@ -1514,14 +1514,40 @@ seed_scale_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, 
 }
 
 // Exact forces of base cases (Fig. 4 leaf triples), a warp per item: for each
-// distinct slot, a lane per particle of that leaf sums grad over the partner
-// pairs the canonical case allows, and credits -grad.
+// distinct slot, a lane per particle a of that leaf sums grad_a phi over the
+// partner pairs (b, c) the canonical case allows, and credits -grad. The
+// partner pairs' terms (unit vector, r^-3) are built once per slot in the
+// warp's shared table; a's terms to 8 columns c are held in registers and
+// its term to row b is formed once per row, so the inner loop is the
+// gradient alone. Masked pairs have zero terms and contribute exactly 0.
 constexpr int kForceWarps = 4;
+constexpr int kForceCols = 8;
+struct ForceWarpSmem {
+    float4 ph[3][kTile], pl[3][kTile];  // the three leaves (hi/lo)
+    float4 tab[kTile][kTile];           // partner pair (b, c): (e_bc, rho_bc)
+};
+
+__device__ __forceinline__ float3 grad_from_terms(const PairFY& ab, const PairFY& ac, float4 bc) {
+    const float p1 = ab.ex * ac.ex + ab.ey * ac.ey + ab.ez * ac.ez;
+    const float p2 = ab.ex * bc.x + ab.ey * bc.y + ab.ez * bc.z;
+    const float p3 = ac.ex * bc.x + ac.ey * bc.y + ac.ez * bc.z;
+    const float q = fmaf(5.0f, p1 * p2 * p3, -1.0f);
+    const float R3 = 3.0f * (ab.rho * ac.rho * bc.w);
+    const float su = R3 * ab.y, sv = R3 * ac.y;
+    const float p23 = p2 * p3, p13 = p1 * p3, p12 = p1 * p2;
+    float3 g;
+    g.x = -su * (q * ab.ex - p23 * ac.ex - p13 * bc.x) - sv * (q * ac.ex - p23 * ab.ex - p12 * bc.x);
+    g.y = -su * (q * ab.ey - p23 * ac.ey - p13 * bc.y) - sv * (q * ac.ey - p23 * ab.ey - p12 * bc.y);
+    g.z = -su * (q * ab.ez - p23 * ac.ez - p13 * bc.z) - sv * (q * ac.ez - p23 * ab.ez - p12 * bc.z);
+    return g;
+}
+
 __global__ void __launch_bounds__(kForceWarps * 32)
 base_forces_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_t N,
                    const int4* __restrict__ items, int64_t n_items, double* __restrict__ acc3) {
-    __shared__ float4 sh[kForceWarps][3][kTile], sl[kForceWarps][3][kTile];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    ForceWarpSmem& sm = reinterpret_cast<ForceWarpSmem*>(smem_raw)[w];
     const int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (item >= n_items) return;
     const int4 t = items[item];
@@ -1533,8 +1559,8 @@ base_forces_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl,
         int64_t e;
         node_range(L[s], N, b[s], e);
         n[s] = (int)(e - b[s]);
-        sh[w][s][lane] = lane < n[s] ? xh[b[s] + lane] : z4;
-        sl[w][s][lane] = lane < n[s] ? xl[b[s] + lane] : z4;
+        sm.ph[s][lane] = lane < n[s] ? xh[b[s] + lane] : z4;
+        sm.pl[s][lane] = lane < n[s] ? xl[b[s] + lane] : z4;
     }
     __syncwarp();
     for (int s = 0; s < 3; ++s) {
@@ -1542,24 +1568,48 @@ base_forces_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl,
         const int o1 = s == 0 ? 1 : 0, o2 = s == 2 ? 1 : 2;
         const bool same = L[o1] == L[o2];
         const bool ex1 = L[o1] == L[s], ex2 = L[o2] == L[s];
-        const float4 ah = sh[w][s][lane], al = sl[w][s][lane];
-        double gx = 0.0, gy = 0.0, gz = 0.0;
-        for (int bi = 0; bi < n[o1]; ++bi) {
-            float rx = 0.f, ry = 0.f, rz = 0.f;
-            const bool skip_b = ex1 && bi == lane;
-            for (int ci = same ? bi + 1 : 0; ci < n[o2]; ++ci) {
-                if (skip_b || (ex2 && ci == lane)) continue;
-                const float3 g = grad_first_fp32(ah, al, sh[w][o1][bi], sl[w][o1][bi],
-                                                 sh[w][o2][ci], sl[w][o2][ci]);
-                rx += g.x;
-                ry += g.y;
-                rz += g.z;
+        __syncwarp();  // the previous pass is done with the table
+        for (int e = lane; e < kTile * kTile; e += 32) {
+            const int bi = e >> 5, ci = e & 31;
+            const bool v = bi < n[o1] && ci < n[o2] && (!same || bi < ci);
+            float4 ent = z4;
+            if (v) {
+                const PairFY bc = pair_sample_y(sm.ph[o1][bi], sm.pl[o1][bi], sm.ph[o2][ci],
+                                                sm.pl[o2][ci]);
+                ent = make_float4(bc.ex, bc.ey, bc.ez, bc.rho);
             }
-            gx += (double)rx;
-            gy += (double)ry;
-            gz += (double)rz;
+            sm.tab[bi][ci] = ent;
         }
-        if (lane < n[s]) {
+        __syncwarp();
+        const float4 ah = sm.ph[s][lane], al = sm.pl[s][lane];
+        const bool act = lane < n[s];
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int cb = 0; cb < n[o2]; cb += kForceCols) {
+            PairFY ac[kForceCols];
+#pragma unroll
+            for (int q = 0; q < kForceCols; ++q) {
+                const int ci = cb + q;
+                const bool v = act && ci < n[o2] && !(ex2 && ci == lane);
+                ac[q] = pair_sample_y(ah, al, sm.ph[o2][ci & 31], sm.pl[o2][ci & 31]);
+                if (!v) ac[q] = PairFY{0.f, 0.f, 0.f, 0.f, 0.f};
+            }
+            for (int bi = 0; bi < n[o1]; ++bi) {
+                PairFY ab = pair_sample_y(ah, al, sm.ph[o1][bi], sm.pl[o1][bi]);
+                if (!act || (ex1 && bi == lane)) ab = PairFY{0.f, 0.f, 0.f, 0.f, 0.f};
+                float rx = 0.f, ry = 0.f, rz = 0.f;
+#pragma unroll
+                for (int q = 0; q < kForceCols; ++q) {
+                    const float3 g = grad_from_terms(ab, ac[q], sm.tab[bi][(cb + q) & 31]);
+                    rx += g.x;
+                    ry += g.y;
+                    rz += g.z;
+                }
+                gx += (double)rx;
+                gy += (double)ry;
+                gz += (double)rz;
+            }
+        }
+        if (act) {
             const int64_t a = b[s] + lane;
             atomicAdd(&acc3[3 * a], -gx);
             atomicAdd(&acc3[3 * a + 1], -gy);
@@ -2077,6 +2127,10 @@ static mbm_status tree_solve(mbm_ctx* ctx, const double* X, int64_t N, double ep
     const size_t bsm = sizeof(BaseSmem);
     MBM_CUDA_TRY(cudaFuncSetAttribute((const void*)base_group_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm));
+    if (F)
+        MBM_CUDA_TRY(cudaFuncSetAttribute((const void*)base_forces_kernel,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(sizeof(ForceWarpSmem) * kForceWarps)));
     int base_per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&base_per_sm, base_group_kernel,
                                                       kBaseWarps * 32, bsm) != cudaSuccess ||
@@ -2098,8 +2152,9 @@ static mbm_status tree_solve(mbm_ctx* ctx, const double* X, int64_t N, double ep
         base_key_kernel<<<grid_of(n, 256), 256, 0, s>>>(basel, n, N, first_leaf, d, bkey, bval,
                                                         ctr + 12);
         if (F) {  // exact forces of each leaf triple, a warp each
-            base_forces_kernel<<<grid_of(n * 32, kForceWarps * 32), kForceWarps * 32, 0, s>>>(
-                tree->xh, tree->xl, N, basel, n, pt_acc3);
+            base_forces_kernel<<<grid_of(n * 32, kForceWarps * 32), kForceWarps * 32,
+                                 sizeof(ForceWarpSmem) * kForceWarps, s>>>(tree->xh, tree->xl, N,
+                                                                          basel, n, pt_acc3);
             MBM_CUDA_TRY(cudaGetLastError());
             if (tm.on) {
                 cudaEventRecord(b, s);
