@@ -40,6 +40,10 @@ METRIC = "AT triples/s (exhaustive) & particles/s at eps=1e-2 vs plain FP64; p50
 WORKLOAD = "exh32_n32768"
 N_MAIN = 32768
 FLOPS_PER_TRIPLE_FP32 = 23   # counted from the inner loop (FMA = 2), see csrc/tile_fp32.cuh
+# adjoint (gather form): 43 FLOPs per evaluation of grad_i phi (9 dot-product
+# operations = 15 FLOPs, products and coefficients 22, accumulations 6; FMA = 2,
+# csrc/adjoint.cu), three evaluations per unordered triple
+FLOPS_PER_TRIPLE_ADJOINT = 3 * 43
 FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one exh_fp32_pt_kernel launch on
 # the N = 32 768 set (ncu, one pass; the command is in
@@ -249,6 +253,20 @@ def bench_tree(api, inputs, torch, dev, r64, np, workload="gmm4_n65536", eps_lis
     return out
 
 
+def fp32_peak_tflops(torch, dev):
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(_peaks().get("sm_max_mhz", 2070.0))
+    return props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+
+
+def forces_roofline(rate, torch, dev):
+    peak = fp32_peak_tflops(torch, dev)
+    achieved = rate * FLOPS_PER_TRIPLE_ADJOINT / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "kernel": "adjoint_kernel<float>",
+            "flops_per_triple": FLOPS_PER_TRIPLE_ADJOINT, "traffic": None}
+
+
 def bench_forces(api, inputs, torch, dev):
     n = 16384
     X = inputs.uniform_cube(n, 32.0 * (n / 65536) ** (1 / 3), 0.5, 4)
@@ -260,6 +278,7 @@ def bench_forces(api, inputs, torch, dev):
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return {"n": n, "triples_per_s": triples(n) / dt, "s": dt,
+            "roofline": forces_roofline(triples(n) / dt, torch, dev),
             "note": "gather form: each unordered triple evaluated once per member"}
 
 
@@ -427,7 +446,8 @@ def run_forces_only(args):
     F = api.forces(Xd, mode="fp32")
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    rep["exhaustive_fp32"] = {"s": dt, "triples_per_s": triples(n) / dt}
+    rep["exhaustive_fp32"] = {"s": dt, "triples_per_s": triples(n) / dt,
+                              "roofline": forces_roofline(triples(n) / dt, torch, dev)}
     print(json.dumps({"progress": rep}), flush=True)
     Fe = F.cpu().numpy()
     for eps in (1e-2,):
