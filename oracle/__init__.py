@@ -20,7 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
-_SOURCES = ["at_oracle.c", "tree_oracle.c"]
+_SOURCES = ["at_oracle.c", "tree_oracle.c", "farfield_oracle.c"]
 _LIB = None
 _LOCK = threading.Lock()
 
