@@ -467,6 +467,89 @@ def run_forces_only(args):
     return 0
 
 
+def farfield_flops_per_query(p):
+    """FP32 operations of one query point in ff_eval_kernel<p>, counted from its
+    loops: 14 Taylor recurrences (per coefficient of degree k >= 1: the v_d t
+    products and their sum, the t_{a - 2e_d} sum, and the scaled combination)
+    and 10 contractions (per padded row of L columns: L multiply-adds, the two
+    partial sums, and the multiply-add with t_{a12})."""
+    def n(k):
+        return 0 if k < 0 else (k + 1) * (k + 2) * (k + 3) // 6
+
+    taylor = 0
+    for k in range(1, p + 1):
+        taylor += 2  # the two coefficients of the level
+        for i in range(k, -1, -1):
+            for j in range(k - i, -1, -1):
+                l = k - i - j
+                na = (i > 0) + (j > 0) + (l > 0)
+                nb = (i > 1) + (j > 1) + (l > 1)
+                taylor += 2 * na - 1 + max(nb - 1, 0) + (3 if nb else 1)
+    contract = 0
+    for d in range(p + 1):
+        L = n(p - d)
+        contract += (d + 1) * (d + 2) // 2 * (2 * L + 3)
+    return 14 * taylor + 10 * contract
+
+
+def run_farfield_only(args):
+    """The three-body far-field expansion (mbm_farfield3) at orders 0..6 on
+    2^20 query points against two source clusters of 4 096 points each
+    (Gaussian, radius 0.35, centre distances 4-6.4: the separations of pruned
+    node triples), timed with CUDA events on the launching stream; accuracy of
+    64 sampled queries against the exact double sum (FP64 oracle)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from oracle import farfield as off
+    from paper_1105_2769_gb300 import api
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(22)
+    n_src, nq = 4096, 1 << 20
+    Y2 = rng.normal(size=(n_src, 3)) * 0.35 + np.array([4.0, 0.3, -0.2])
+    Y3 = rng.normal(size=(n_src, 3)) * 0.35 + np.array([0.5, 4.0, 1.6])
+    Xq = rng.normal(size=(nq, 3)) * 0.35
+    d = [torch.from_numpy(a).to(dev) for a in (Xq, Y2, Y3)]
+    idx = rng.choice(nq, 64, replace=False)
+    t0 = time.perf_counter()
+    exact = off.pairset_sum(Xq[idx], Y2, Y3)
+    t_exact = time.perf_counter() - t0
+    peak = fp32_peak_tflops(torch, dev)
+    rows = []
+    for p in range(7):
+        out = api.farfield3(*d, p)
+        for _ in range(3):
+            api.farfield3(*d, p)
+        s = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        ev0.record(s)
+        for _ in range(reps):
+            api.farfield3(*d, p, validate=False)
+        ev1.record(s)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        got = out.cpu().numpy()[idx]
+        ref = off.farfield3(Xq[idx], Y2, Y3, p)
+        rate = nq / (ms * 1e-3)
+        fl = farfield_flops_per_query(p)
+        rows.append({"p": p, "ms": ms, "queries_per_s": rate,
+                     "max_rel_err_vs_exact": float(np.max(np.abs(got - exact) / np.abs(exact))),
+                     "max_rel_dev_vs_oracle_expansion": float(np.max(np.abs(got - ref) / np.abs(ref))),
+                     "roofline": {"bound": "alu", "achieved": rate * fl / 1e12, "peak": peak,
+                                  "unit": "TFLOP/s", "frac": rate * fl / 1e12 / peak,
+                                  "kernel": f"ff_eval_kernel<{p}> (whole call timed)",
+                                  "flops_per_query": fl, "traffic": None}})
+        print(json.dumps({"progress": rows[-1]}), flush=True)
+    pair_rate = len(idx) * n_src * n_src / t_exact
+    print(json.dumps({"report": "farfield", "queries": nq, "sources": [n_src, n_src],
+                      "workload": "Gaussian clusters radius 0.35 at centre distances 4-6.4, seed 22",
+                      "exact_pairs_per_s_cpu_oracle": pair_rate,
+                      "exact_cores": oracle.max_threads(), "rows": rows}))
+    return 0
+
+
 def run_paper_shape(args):
     """The paper's experiment shapes (Sec. 6) on this GPU: uniform cube, unit
     ball and thin shell ("annulus"), tree solves at eps 1e-1/1e-2/1e-3 and
@@ -552,6 +635,8 @@ def main():
     ap.add_argument("--forces-only", action="store_true",
                     help="exhaustive and tree forces of the N = 65 536 force workload")
     ap.add_argument("--forces-n", type=int, default=65536)
+    ap.add_argument("--farfield-only", action="store_true",
+                    help="far-field expansion orders 0..6 on 2^20 queries")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -563,6 +648,8 @@ def main():
         return run_serving_only(args)
     if args.forces_only:
         return run_forces_only(args)
+    if args.farfield_only:
+        return run_farfield_only(args)
 
     import numpy as np
     import torch

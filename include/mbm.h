@@ -175,6 +175,36 @@ mbm_status mbm_potential_sampled(mbm_ctx* ctx, const double* X_dev, int64_t N,
                                  mbm_stream_t stream);
 
 /*
+ * Three-body far-field expansion (Sec. 3.2, Eq.
+ * truncated_three_body_farfield_expansion) of Axilrod-Teller sums: for each
+ * query point x (Xq_dev, nq x 3 FP64, device) the p-th order expansion of
+ *
+ *   Phi(x; P2 x P3) = sum_{y2 in P2} sum_{y3 in P3} phi(x, y2, y3)
+ *
+ * about the centres of mass c2, c3 of the source sets P2 (Y2_dev, n2 x 3) and
+ * P3 (Y3_dev, n3 x 3), with the far-field moments of Sec. 3.1 up to order p.
+ * Axilrod-Teller enters as ten products of pairwise powers (law of cosines).
+ * p = 0 is the monopole n2 n3 phi(x, c2, c3) of the p = 0 rule (Sec. 4); the
+ * error falls with p where the query and source sets are well separated
+ * (|y - c| small against the distances between x, c2 and c3).
+ *   out_dev: caller-owned FP64[nq] on the device.
+ *   p: 0..6. Moments and the source-dependent coefficients are FP64; each
+ *   query point is evaluated in FP32 arithmetic with an FP64 sum over the
+ *   ten product terms.
+ *   n2 == 0 or n3 == 0: the double sum is empty, out = 0.
+ *   The sets are taken as given: the caller keeps x out of P2 and P3 (as for
+ *   distinct tree nodes); P2 and P3 may share points, but not a centre.
+ *   validate = 1 synchronises `stream` and reports a non-finite coordinate
+ *   or a query point at a centre, or c2 == c3 (the expansion is undefined
+ *   there), as MBM_EINVAL; with validate = 0 such outputs are NaN or Inf.
+ * Errors: MBM_EINVAL (bad p, NULL pointer, negative size), MBM_EBUDGET,
+ * MBM_ENOMEM. Scratch: a few hundred KB from the context's arena.
+ */
+mbm_status mbm_farfield3(mbm_ctx* ctx, const double* Xq_dev, int64_t nq, const double* Y2_dev,
+                         int64_t n2, const double* Y3_dev, int64_t n3, int p, int validate,
+                         double* out_dev, mbm_stream_t stream);
+
+/*
  * Build the spatial tree of Sec. 3 (bottom-up phase) for X_dev (N x 3 FP64,
  * device): Morton-ordered permutation, balanced node ranges of at most
  * cfg->leaf_size points, FP64 bounding boxes and centres of mass, and the

@@ -100,6 +100,7 @@ SIGNATURES = {
                              ctypes.POINTER(ctypes.c_int32)]),
     "mbm_tree_export": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "mbm_potential_sampled": (_int, [_vp, _vp, _i64, _vp, _i64, _vp, _vp]),
+    "mbm_farfield3": (_int, [_vp, _vp, _i64, _vp, _i64, _vp, _i64, _int, _int, _vp, _vp]),
     "mbm_server_create": (_int, [_int, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(_vp)]),
     "mbm_server_destroy": (_int, [_vp]),
     "mbm_submit": (_int, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),

@@ -208,6 +208,23 @@ def potential_sampled(X: torch.Tensor, idx, ctx: Context | None = None) -> torch
     return out
 
 
+def farfield3(Xq: torch.Tensor, Y2: torch.Tensor, Y3: torch.Tensor, p: int,
+              ctx: Context | None = None, validate: bool = True) -> torch.Tensor:
+    """p-th order three-body far-field expansion (Sec. 3.2) at each query point
+    of sum_{y2 in Y2} sum_{y3 in Y3} phi(x, y2, y3), about the centres of mass."""
+    Xq, Y2, Y3 = (_check_points(t) for t in (Xq, Y2, Y3))
+    if not (Xq.device == Y2.device == Y3.device):
+        raise ValueError("query and source points must be on one device")
+    ctx = ctx or default_context(Xq.device.index)
+    out = torch.empty(Xq.shape[0], dtype=torch.float64, device=Xq.device)
+    _lib.check(_lib.load().mbm_farfield3(ctx.handle, ctypes.c_void_p(Xq.data_ptr()), Xq.shape[0],
+                                         ctypes.c_void_p(Y2.data_ptr()), Y2.shape[0],
+                                         ctypes.c_void_p(Y3.data_ptr()), Y3.shape[0], int(p),
+                                         int(bool(validate)), ctypes.c_void_p(out.data_ptr()),
+                                         _stream_handle()))
+    return out
+
+
 def forces(X: torch.Tensor, mode="fp32", eps: float = 0.0, alpha: float = 0.0,
            ctx: Context | None = None, config: _lib.Config | None = None, tree=None,
            stats: bool = False, tuple_counts: torch.Tensor | None = None):

@@ -1,0 +1,503 @@
+// Three-body far-field expansion of Axilrod-Teller sums (§3.2, Eq.
+// truncated_three_body_farfield_expansion), orders p = 0..6.
+//
+// For query points x and two source sets P2, P3 with centres of mass c2, c3
+// the p-th order expansion of
+//   Phi(x; P2 x P3) = sum_{y2 in P2} sum_{y3 in P3} phi(x, y2, y3).
+//
+// Axilrod-Teller as products of pairwise powers. With a = |x - y2|^2,
+// b = |x - y3|^2, c = |y2 - y3|^2 the law of cosines turns the cosine product
+// into (b + c - a)(a + c - b)(a + b - c) / (8abc), so
+//   phi = (abc)^(-3/2) + (3/8) (b + c - a)(a + c - b)(a + b - c) (abc)^(-5/2).
+// The cubic has ten monomials a^i b^j c^k: -a^3 - b^3 - c^3 - 2abc and the six
+// a^2 b-type terms with coefficient 1. The abc monomial and the (abc)^(-3/2)
+// term share exponents, so phi is a sum of ten products
+//   w_m (a)^(s12_m) (b)^(s13_m) (c)^(s23_m),  s = i - 5/2 etc.,
+// each a product of pairwise functions g(v) = (v.v)^s, which is the form the
+// paper's expansion is written for. The expansion of the sum is the sum of
+// the ten expansions.
+//
+// Factorisation used here. With t^s_a(v) = D^a (v.v)^s / a! (Taylor
+// coefficients) the expansion of one product term is
+//   sum_{a12, a13} t^{s12}_{a12}(x - c2) t^{s13}_{a13}(x - c3) K[a12, a13],
+//   K[a12, a13] = w a12! a13! sum_{a23} sum_{b <= a23} C(a12 + b, a12) C(a13 + a23 - b, a13)
+//                 (-1)^|b| M_{a12 + b}(P2) M_{a13 + a23 - b}(P3) D^{a23} (w23.w23)^{s23}
+// over |a12| + |a13| + |a23| <= p, w23 = c2 - c3, with the far-field moments
+// of §3.1, M_a(P, c) = sum_y (-1)^|a| (y - c)^a / a!. This is the paper's
+// quadruple sum with a = a12 + a13 + a23 regrouped: K holds everything that
+// does not depend on x, so it is formed once per call (FP64), and a query
+// point costs the Taylor coefficients of four powers at x - c2 and at x - c3
+// and one contraction with K per product term (FP32 arithmetic, K in shared
+// memory, FP64 sum over the ten terms) instead of the O(p^6) sum per point.
+//
+// Taylor coefficients come from a recurrence: f = (v.v)^s satisfies
+// (v.v) grad f = 2 s v f; the coefficient of t^a on both sides at v0 + t gives
+//   |a| |v0|^2 t_a = (2s - 2|a| + 2) sum_d v0_d t_{a - e_d} + (2s - |a| + 2) sum_d t_{a - 2 e_d}.
+//
+// Kernels, in stream order: coordinate sums per block of each source set;
+// moments per block about the centre; one block finishing the moments, the
+// centres and the Taylor coefficients of the four powers at c2 - c3; K, one
+// block per row a12; the query sweep. Every reduction runs in a fixed order,
+// so results do not depend on scheduling.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "mbm_internal.h"
+
+namespace {
+
+constexpr int kPMax = 6;
+constexpr int kTerms = 10;
+constexpr int kSumThreads = 256;
+constexpr int kMomThreads = 128;
+constexpr int kEvalThreads = 128;
+
+// number of multi-indices with |a| <= k
+__host__ __device__ constexpr int ff_n(int k) { return k < 0 ? 0 : (k + 1) * (k + 2) * (k + 3) / 6; }
+// position of (i, j, l): by degree, then i descending, then j descending
+__host__ __device__ constexpr int ff_idx(int i, int j, int l) {
+    return ff_n(i + j + l - 1) + (j + l) * (j + l + 1) / 2 + l;
+}
+__host__ __device__ constexpr int pad4(int x) { return (x + 3) / 4 * 4; }
+// floats of K per product term at order P: rows a12 of degree d hold the
+// columns a13 with |a13| <= P - d, padded to a multiple of four
+__host__ __device__ constexpr int k_stride(int P) {
+    int s = 0;
+    for (int d = 0; d <= P; ++d) s += (d + 1) * (d + 2) / 2 * pad4(ff_n(P - d));
+    return s;
+}
+
+struct MultiIndexTable {
+    unsigned char a[ff_n(kPMax)][3];
+};
+constexpr MultiIndexTable make_table() {
+    MultiIndexTable t{};
+    int n = 0;
+    for (int k = 0; k <= kPMax; ++k)
+        for (int i = k; i >= 0; --i)
+            for (int j = k - i; j >= 0; --j) {
+                t.a[n][0] = (unsigned char)i;
+                t.a[n][1] = (unsigned char)j;
+                t.a[n][2] = (unsigned char)(k - i - j);
+                ++n;
+            }
+    return t;
+}
+__constant__ MultiIndexTable kAl = make_table();
+
+// The ten product terms as 2 s12, 2 s13, 2 s23 and w, grouped by s12 in the
+// order the query sweep visits them.
+__constant__ int kS23x2[kTerms] = {-5, -5, -3, -5, -3, -1, -5, -3, -1, 1};
+__constant__ double kW[kTerms] = {-0.375, 0.375, 0.375, 0.375, 0.25,
+                                  0.375,  -0.375, 0.375, 0.375, -0.375};
+
+__device__ __forceinline__ double fact_d(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+__device__ __forceinline__ double binom_d(int n, int k) {
+    double c = 1.0;
+    for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+    return c;
+}
+
+// ---------------------------------------------------------------- sums
+// part[set][b][3]: coordinate sums of block b's chunk of each source set.
+__global__ void __launch_bounds__(kSumThreads)
+ff_sums_kernel(const double* __restrict__ Y2, int64_t n2, const double* __restrict__ Y3, int64_t n3,
+               int nb, double* __restrict__ part, int* __restrict__ flags) {
+    __shared__ double red[3][kSumThreads];
+    const int set = blockIdx.y;
+    const double* Y = set ? Y3 : Y2;
+    const int64_t n = set ? n3 : n2;
+    const int64_t chunk = (n + nb - 1) / nb;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk;
+    const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+    double s[3] = {0.0, 0.0, 0.0};
+    bool bad = false;
+    for (int64_t i = b0 + threadIdx.x; i < b1; i += kSumThreads)
+        for (int d = 0; d < 3; ++d) {
+            const double v = Y[3 * i + d];
+            bad |= !isfinite(v);
+            s[d] += v;
+        }
+    if (bad) atomicOr(flags, MBM_FLAG_NONFINITE);
+    for (int d = 0; d < 3; ++d) red[d][threadIdx.x] = s[d];
+    __syncthreads();
+    for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int d = 0; d < 3; ++d) red[d][threadIdx.x] += red[d][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[((int64_t)set * nb + blockIdx.x) * 3 + threadIdx.x] = red[threadIdx.x][0];
+}
+
+// ---------------------------------------------------------------- moments
+// mpart[set][b][a] = sum over block b's chunk of (y - c)^a / a! (no sign yet).
+__global__ void __launch_bounds__(kMomThreads)
+ff_moments_kernel(const double* __restrict__ Y2, int64_t n2, const double* __restrict__ Y3, int64_t n3,
+                  int nb, int p, const double* __restrict__ part, double* __restrict__ mpart) {
+    __shared__ double pw[kMomThreads][3][kPMax + 1];  // (y_d - c_d)^k / k! of staged points
+    __shared__ double cen[3];
+    const int set = blockIdx.y;
+    const double* Y = set ? Y3 : Y2;
+    const int64_t n = set ? n3 : n2;
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[((int64_t)set * nb + b) * 3 + threadIdx.x];
+        cen[threadIdx.x] = s / (double)n;
+    }
+    __syncthreads();
+    const int na = ff_n(p);
+    const int t = threadIdx.x;
+    const int ai = t < na ? kAl.a[t][0] : 0, aj = t < na ? kAl.a[t][1] : 0,
+              al = t < na ? kAl.a[t][2] : 0;
+    const int64_t chunk = (n + nb - 1) / nb;
+    const int64_t b0 = (int64_t)blockIdx.x * chunk;
+    const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+    double acc = 0.0;
+    for (int64_t s0 = b0; s0 < b1; s0 += kMomThreads) {
+        const int64_t i = s0 + t;
+        if (i < b1) {
+            for (int d = 0; d < 3; ++d) {
+                const double v = Y[3 * i + d] - cen[d];
+                double m = 1.0;
+                pw[t][d][0] = 1.0;
+                for (int k = 1; k <= p; ++k) {
+                    m = m * v / k;
+                    pw[t][d][k] = m;
+                }
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)(b1 - s0 < kMomThreads ? b1 - s0 : kMomThreads);
+        if (t < na)
+            for (int q = 0; q < cnt; ++q) acc += pw[q][0][ai] * pw[q][1][aj] * pw[q][2][al];
+        __syncthreads();
+    }
+    if (t < na) mpart[((int64_t)set * nb + blockIdx.x) * ff_n(kPMax) + t] = acc;
+}
+
+// ---------------------------------------------------------------- finish
+// fin layout (doubles): M2[84], M3[84], D23[4][84] (D^a (w.w)^s for 2s = 1, -1,
+// -3, -5), c2[3], c3[3].
+constexpr int kFinM2 = 0, kFinM3 = ff_n(kPMax), kFinD = 2 * ff_n(kPMax),
+              kFinC = 6 * ff_n(kPMax), kFinDoubles = 6 * ff_n(kPMax) + 8;
+
+__global__ void __launch_bounds__(kMomThreads)
+ff_finish_kernel(int64_t n2, int64_t n3, int nb, int p, const double* __restrict__ part,
+                 const double* __restrict__ mpart, double* __restrict__ fin, int* __restrict__ flags) {
+    __shared__ double w[3];
+    const int na = ff_n(p);
+    const int t = threadIdx.x;
+    if (t < 6) {
+        const int set = t / 3, d = t % 3;
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[((int64_t)set * nb + b) * 3 + d];
+        fin[kFinC + t] = s / (double)(set ? n3 : n2);
+    }
+    for (int q = t; q < 2 * na; q += kMomThreads) {
+        const int set = q / na, a = q % na;
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += mpart[((int64_t)set * nb + b) * ff_n(kPMax) + a];
+        const int deg = kAl.a[a][0] + kAl.a[a][1] + kAl.a[a][2];
+        fin[(set ? kFinM3 : kFinM2) + a] = (deg & 1) ? -s : s;
+    }
+    __syncthreads();
+    if (t < 3) w[t] = fin[kFinC + t] - fin[kFinC + 3 + t];
+    __syncthreads();
+    const double r2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    if (t == 0 && !(r2 > 0.0)) atomicOr(flags, MBM_FLAG_COINCIDENT);
+    if (t < 4) {  // Taylor coefficients of (w.w)^s at w by the recurrence, then D = a! t
+        const int s2 = 1 - 2 * t;  // 2s = 1, -1, -3, -5
+        double* D = fin + kFinD + t * ff_n(kPMax);
+        const double r = sqrt(r2);
+        D[0] = pow(r, (double)s2);
+        for (int q = 1; q < na; ++q) {
+            const int i = kAl.a[q][0], j = kAl.a[q][1], l = kAl.a[q][2], k = i + j + l;
+            double A = 0.0, B = 0.0;
+            if (i > 0) A += w[0] * D[ff_idx(i - 1, j, l)];
+            if (j > 0) A += w[1] * D[ff_idx(i, j - 1, l)];
+            if (l > 0) A += w[2] * D[ff_idx(i, j, l - 1)];
+            if (i > 1) B += D[ff_idx(i - 2, j, l)];
+            if (j > 1) B += D[ff_idx(i, j - 2, l)];
+            if (l > 1) B += D[ff_idx(i, j, l - 2)];
+            D[q] = ((s2 - 2 * k + 2) * A + (s2 - k + 2) * B) / (k * r2);
+        }
+        for (int q = 0; q < na; ++q)
+            D[q] *= fact_d(kAl.a[q][0]) * fact_d(kAl.a[q][1]) * fact_d(kAl.a[q][2]);
+    }
+}
+
+// ---------------------------------------------------------------- K
+// One block per row a12; thread columns a13. K[m][row offset + col] in FP32.
+__global__ void __launch_bounds__(kMomThreads)
+ff_k_kernel(int p, const double* __restrict__ fin, float* __restrict__ K) {
+    const int r = blockIdx.x;  // a12 index
+    const int i12 = kAl.a[r][0], j12 = kAl.a[r][1], l12 = kAl.a[r][2], d12 = i12 + j12 + l12;
+    const int L = ff_n(p - d12);
+    int off = 0;
+    for (int d = 0; d < d12; ++d) off += (d + 1) * (d + 2) / 2 * pad4(ff_n(p - d));
+    off += (r - ff_n(d12 - 1)) * pad4(L);
+    const int stride = k_stride(p);
+    const double* M2 = fin + kFinM2;
+    const double* M3 = fin + kFinM3;
+    for (int c = threadIdx.x; c < pad4(L); c += kMomThreads) {
+        double acc[kTerms];
+        for (int m = 0; m < kTerms; ++m) acc[m] = 0.0;
+        if (c < L) {
+            const int i13 = kAl.a[c][0], j13 = kAl.a[c][1], l13 = kAl.a[c][2];
+            const int d13 = i13 + j13 + l13;
+            for (int q = 0; q < ff_n(p - d12 - d13); ++q) {  // a23
+                const int i23 = kAl.a[q][0], j23 = kAl.a[q][1], l23 = kAl.a[q][2];
+                double S = 0.0;
+                for (int ib = 0; ib <= i23; ++ib)
+                    for (int jb = 0; jb <= j23; ++jb)
+                        for (int lb = 0; lb <= l23; ++lb) {
+                            const int gi = i12 + ib, gj = j12 + jb, gl = l12 + lb;  // a12 + b
+                            const int hi = i13 + i23 - ib, hj = j13 + j23 - jb,
+                                      hl = l13 + l23 - lb;  // a13 + a23 - b
+                            const double cb = binom_d(gi, i12) * binom_d(gj, j12) * binom_d(gl, l12) *
+                                              binom_d(hi, i13) * binom_d(hj, j13) * binom_d(hl, l13);
+                            const double v = cb * M2[ff_idx(gi, gj, gl)] * M3[ff_idx(hi, hj, hl)];
+                            S += ((ib + jb + lb) & 1) ? -v : v;
+                        }
+                for (int m = 0; m < kTerms; ++m) {
+                    const int sidx = (1 - kS23x2[m]) / 2;  // 2s = 1, -1, -3, -5 -> 0..3
+                    acc[m] += S * fin[kFinD + sidx * ff_n(kPMax) + q];
+                }
+            }
+            const double f = fact_d(i12) * fact_d(j12) * fact_d(l12) * fact_d(i13) * fact_d(j13) *
+                             fact_d(l13);
+            for (int m = 0; m < kTerms; ++m) acc[m] *= kW[m] * f;
+        }
+        for (int m = 0; m < kTerms; ++m) K[m * stride + off + c] = (float)acc[m];
+    }
+}
+
+// ---------------------------------------------------------------- query sweep
+// Taylor coefficients of (v.v)^(S2/2) at v, |a| <= P, in FP32 registers.
+template <int P, int S2>
+__device__ __forceinline__ void taylor(float vx, float vy, float vz, float r2inv, float r0,
+                                       float (&t)[ff_n(P)]) {
+    t[0] = r0;
+#pragma unroll
+    for (int k = 1; k <= P; ++k) {
+        const float ca = (float)(S2 - 2 * k + 2) / (float)k * r2inv;
+        const float cb = (float)(S2 - k + 2) / (float)k * r2inv;
+#pragma unroll
+        for (int i = k; i >= 0; --i)
+#pragma unroll
+            for (int j = k - i; j >= 0; --j) {
+                const int l = k - i - j;
+                float A = 0.f, B = 0.f;
+                if (i > 0) A = fmaf(vx, t[ff_idx(i - 1, j, l)], A);
+                if (j > 0) A = fmaf(vy, t[ff_idx(i, j - 1, l)], A);
+                if (l > 0) A = fmaf(vz, t[ff_idx(i, j, l - 1)], A);
+                if (i > 1) B += t[ff_idx(i - 2, j, l)];
+                if (j > 1) B += t[ff_idx(i, j - 2, l)];
+                if (l > 1) B += t[ff_idx(i, j, l - 2)];
+                t[ff_idx(i, j, l)] = (S2 - k + 2 == 0) ? ca * A : fmaf(cb, B, ca * A);
+            }
+    }
+}
+
+// sum_{a12, a13} tu[a12] tv[a13] K[a12, a13] over the padded row layout
+template <int P>
+__device__ __forceinline__ float contract(const float (&tu)[ff_n(P)], const float (&tv)[ff_n(P)],
+                                          const float* __restrict__ Km) {
+    float acc = 0.f;
+    int off = 0;
+#pragma unroll
+    for (int d = 0; d <= P; ++d) {
+        const int L = ff_n(P - d);
+#pragma unroll
+        for (int r = ff_n(d - 1); r < ff_n(d); ++r) {
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int q = 0; q < pad4(L) / 4; ++q) {
+                const float4 k4 = *reinterpret_cast<const float4*>(Km + off + 4 * q);
+                s0 = fmaf(tv[4 * q], k4.x, s0);
+                if (4 * q + 1 < L) s1 = fmaf(tv[4 * q + 1], k4.y, s1);
+                if (4 * q + 2 < L) s0 = fmaf(tv[4 * q + 2], k4.z, s0);
+                if (4 * q + 3 < L) s1 = fmaf(tv[4 * q + 3], k4.w, s1);
+            }
+            acc = fmaf(tu[r], s0 + s1, acc);
+            off += pad4(L);
+        }
+    }
+    return acc;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kEvalThreads)
+ff_eval_kernel(const double* __restrict__ Xq, int64_t nq, const float* __restrict__ Kg,
+               const double* __restrict__ fin, double* __restrict__ out, int* __restrict__ flags) {
+    extern __shared__ float4 smem4[];
+    float* Ks = reinterpret_cast<float*>(smem4);
+    constexpr int kStride = k_stride(P);
+    for (int q = threadIdx.x; q < kTerms * kStride / 4; q += kEvalThreads)
+        smem4[q] = reinterpret_cast<const float4*>(Kg)[q];
+    __syncthreads();
+    const double c2x = fin[kFinC], c2y = fin[kFinC + 1], c2z = fin[kFinC + 2];
+    const double c3x = fin[kFinC + 3], c3y = fin[kFinC + 4], c3z = fin[kFinC + 5];
+    for (int64_t i = (int64_t)blockIdx.x * kEvalThreads + threadIdx.x; i < nq;
+         i += (int64_t)gridDim.x * kEvalThreads) {
+        const double x = Xq[3 * i], y = Xq[3 * i + 1], z = Xq[3 * i + 2];
+        const double ux = x - c2x, uy = y - c2y, uz = z - c2z;
+        const double vx = x - c3x, vy = y - c3y, vz = z - c3z;
+        const double ru2 = ux * ux + uy * uy + uz * uz, rv2 = vx * vx + vy * vy + vz * vz;
+        if (!(ru2 > 0.0) || !(rv2 > 0.0) || !isfinite(ru2 + rv2)) {
+            atomicOr(flags, isfinite(ru2 + rv2) ? MBM_FLAG_COINCIDENT : MBM_FLAG_NONFINITE);
+            out[i] = __longlong_as_double(0x7ff8000000000000ll);
+            continue;
+        }
+        const double riu = rsqrt(ru2), riv = rsqrt(rv2);
+        const float fux = (float)ux, fuy = (float)uy, fuz = (float)uz;
+        const float fvx = (float)vx, fvy = (float)vy, fvz = (float)vz;
+        const float u2i = (float)(riu * riu), v2i = (float)(riv * riv);
+        const float ru = (float)(ru2 * riu), rv = (float)(rv2 * riv);  // |u|, |v|
+        const float iu = (float)riu, iv = (float)riv;
+        const float iu3 = (float)(riu * riu * riu), iv3 = (float)(riv * riv * riv);
+        const float iu5 = (float)(riu * riu * riu * riu * riu), iv5 = (float)(riv * riv * riv * riv * riv);
+        float tu[ff_n(P)], tv[ff_n(P)];
+        double acc = 0.0;
+        // terms in the order of kS23x2 / kW: (2 s12, 2 s13)
+        taylor<P, 1>(fux, fuy, fuz, u2i, ru, tu);
+        taylor<P, -5>(fvx, fvy, fvz, v2i, iv5, tv);
+        acc += contract<P>(tu, tv, Ks + 0 * kStride);
+        taylor<P, -1>(fux, fuy, fuz, u2i, iu, tu);
+        taylor<P, -3>(fvx, fvy, fvz, v2i, iv3, tv);
+        acc += contract<P>(tu, tv, Ks + 1 * kStride);
+        taylor<P, -5>(fvx, fvy, fvz, v2i, iv5, tv);
+        acc += contract<P>(tu, tv, Ks + 2 * kStride);
+        taylor<P, -3>(fux, fuy, fuz, u2i, iu3, tu);
+        taylor<P, -1>(fvx, fvy, fvz, v2i, iv, tv);
+        acc += contract<P>(tu, tv, Ks + 3 * kStride);
+        taylor<P, -3>(fvx, fvy, fvz, v2i, iv3, tv);
+        acc += contract<P>(tu, tv, Ks + 4 * kStride);
+        taylor<P, -5>(fvx, fvy, fvz, v2i, iv5, tv);
+        acc += contract<P>(tu, tv, Ks + 5 * kStride);
+        taylor<P, -5>(fux, fuy, fuz, u2i, iu5, tu);
+        taylor<P, 1>(fvx, fvy, fvz, v2i, rv, tv);
+        acc += contract<P>(tu, tv, Ks + 6 * kStride);
+        taylor<P, -1>(fvx, fvy, fvz, v2i, iv, tv);
+        acc += contract<P>(tu, tv, Ks + 7 * kStride);
+        taylor<P, -3>(fvx, fvy, fvz, v2i, iv3, tv);
+        acc += contract<P>(tu, tv, Ks + 8 * kStride);
+        taylor<P, -5>(fvx, fvy, fvz, v2i, iv5, tv);
+        acc += contract<P>(tu, tv, Ks + 9 * kStride);
+        out[i] = acc;
+    }
+}
+
+template <int P>
+cudaError_t launch_eval(const double* Xq, int64_t nq, const float* K, const double* fin, double* out,
+                        int* flags, int num_sms, cudaStream_t s) {
+    const size_t smem = (size_t)kTerms * k_stride(P) * sizeof(float);
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(ff_eval_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ff_eval_kernel<P>,
+                                                                  kEvalThreads, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t want = (nq + kEvalThreads - 1) / kEvalThreads;
+    const int64_t cap = (int64_t)num_sms * (per_sm > 0 ? per_sm : 1);
+    const int grid = (int)(want < cap ? want : cap);
+    ff_eval_kernel<P><<<grid, kEvalThreads, smem, s>>>(Xq, nq, K, fin, out, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_p(int p, const double* Xq, int64_t nq, const float* K, const double* fin,
+                          double* out, int* flags, int num_sms, cudaStream_t s) {
+    switch (p) {
+        case 0: return launch_eval<0>(Xq, nq, K, fin, out, flags, num_sms, s);
+        case 1: return launch_eval<1>(Xq, nq, K, fin, out, flags, num_sms, s);
+        case 2: return launch_eval<2>(Xq, nq, K, fin, out, flags, num_sms, s);
+        case 3: return launch_eval<3>(Xq, nq, K, fin, out, flags, num_sms, s);
+        case 4: return launch_eval<4>(Xq, nq, K, fin, out, flags, num_sms, s);
+        case 5: return launch_eval<5>(Xq, nq, K, fin, out, flags, num_sms, s);
+        default: return launch_eval<6>(Xq, nq, K, fin, out, flags, num_sms, s);
+    }
+}
+
+// blocks per source set for the sums and moments
+int source_blocks(int64_t n2, int64_t n3, int num_sms) {
+    const int64_t n = n2 > n3 ? n2 : n3;
+    int64_t nb = (n + 4095) / 4096;
+    if (nb > num_sms) nb = num_sms;
+    return nb < 1 ? 1 : (int)nb;
+}
+
+}  // namespace
+
+size_t mbm_farfield3_scratch_bytes(int64_t n2, int64_t n3, int num_sms) {
+    const int nb = source_blocks(n2, n3, num_sms);
+    return mbm_align_up((size_t)2 * nb * 3 * sizeof(double), 256) +
+           mbm_align_up((size_t)2 * nb * ff_n(kPMax) * sizeof(double), 256) +
+           mbm_align_up((size_t)kFinDoubles * sizeof(double), 256) +
+           mbm_align_up((size_t)kTerms * k_stride(kPMax) * sizeof(float), 256);
+}
+
+// Enqueue the whole expansion; scratch must hold mbm_farfield3_scratch_bytes.
+cudaError_t launch_farfield3(const double* Xq, int64_t nq, const double* Y2, int64_t n2,
+                             const double* Y3, int64_t n3, int p, double* out, void* scratch,
+                             int* flags, int num_sms, cudaStream_t s) {
+    const int nb = source_blocks(n2, n3, num_sms);
+    char* b = static_cast<char*>(scratch);
+    auto* part = reinterpret_cast<double*>(b);
+    b += mbm_align_up((size_t)2 * nb * 3 * sizeof(double), 256);
+    auto* mpart = reinterpret_cast<double*>(b);
+    b += mbm_align_up((size_t)2 * nb * ff_n(kPMax) * sizeof(double), 256);
+    auto* fin = reinterpret_cast<double*>(b);
+    b += mbm_align_up((size_t)kFinDoubles * sizeof(double), 256);
+    auto* K = reinterpret_cast<float*>(b);
+    ff_sums_kernel<<<dim3(nb, 2), kSumThreads, 0, s>>>(Y2, n2, Y3, n3, nb, part, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ff_moments_kernel<<<dim3(nb, 2), kMomThreads, 0, s>>>(Y2, n2, Y3, n3, nb, p, part, mpart);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ff_finish_kernel<<<1, kMomThreads, 0, s>>>(n2, n3, nb, p, part, mpart, fin, flags);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ff_k_kernel<<<ff_n(p), kMomThreads, 0, s>>>(p, fin, K);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_eval_p(p, Xq, nq, K, fin, out, flags, num_sms, s);
+}
+
+extern "C" mbm_status mbm_farfield3(mbm_ctx* ctx, const double* Xq_dev, int64_t nq,
+                                    const double* Y2_dev, int64_t n2, const double* Y3_dev,
+                                    int64_t n3, int p, int validate, double* out_dev,
+                                    mbm_stream_t stream) {
+    if (!ctx) return mbm_fail(MBM_EINVAL, "ctx is NULL");
+    if (p < 0 || p > kPMax) return mbm_fail(MBM_EINVAL, "order p must be in [0, 6]");
+    if (nq < 0 || n2 < 0 || n3 < 0) return mbm_fail(MBM_EINVAL, "negative size");
+    if (nq > ((int64_t)1 << 40) || n2 > ((int64_t)1 << 40) || n3 > ((int64_t)1 << 40))
+        return mbm_fail(MBM_EINVAL, "size too large (max 2^40)");
+    if (nq > 0 && (!Xq_dev || !out_dev)) return mbm_fail(MBM_EINVAL, "NULL query points or output");
+    if ((n2 > 0 && !Y2_dev) || (n3 > 0 && !Y3_dev)) return mbm_fail(MBM_EINVAL, "NULL source set");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    MBM_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (nq == 0) return MBM_OK;
+    if (n2 == 0 || n3 == 0) {  // empty double sum
+        MBM_CUDA_TRY(cudaMemsetAsync(out_dev, 0, (size_t)nq * sizeof(double), s));
+        return MBM_OK;
+    }
+    MBM_TRY(mbm_scratch_reserve(ctx, mbm_farfield3_scratch_bytes(n2, n3, ctx->num_sms)));
+    MBM_CUDA_TRY(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
+    mbm_time_begin(ctx, s);
+    MBM_CUDA_TRY(launch_farfield3(Xq_dev, nq, Y2_dev, n2, Y3_dev, n3, p, out_dev, ctx->scratch,
+                                  ctx->d_flags, ctx->num_sms, s));
+    mbm_time_end(ctx, s);
+    if (validate) return mbm_check_flags(ctx, s);
+    return MBM_OK;
+}

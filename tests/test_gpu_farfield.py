@@ -1,0 +1,155 @@
+"""The three-body far-field expansion on the GPU (mbm_farfield3) against the
+far-field oracle (§3.2, Eq. truncated_three_body_farfield_expansion).
+
+Bar (written here): the GPU evaluates each query point in FP32 arithmetic
+(Taylor recurrences of four powers at x - c2 and at x - c3, contractions of
+at most 84 x 84 coefficients) with FP64 moments and an FP64 sum over the ten
+product terms. Each term carries a few hundred FP32 roundings relative to its
+own size, and the terms cancel in phi, so the error is measured against the
+magnitudes of the ten product terms summed over the source pairs, scale(x) =
+sum_{y2, y3} sum_m |w_m| a^s12 b^s13 c^s23 (the oracle's pair-set sum with
+|w|): |GPU - oracle| <= 2e-5 scale(x) at every order. The expansion itself is
+the oracle's: its truncation error is not part of the bar; the test also
+checks that the GPU error against the exact double sum falls with p.
+All calls go through the C ABI (ctypes binding).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import farfield as off
+from paper_1105_2769_gb300 import _lib, api, inputs
+
+pytestmark = pytest.mark.gpu
+
+BAR = 2e-5
+
+
+def _merged_abs_terms():
+    s12, s13, s23, w = off.at_product_terms()
+    merged = {}
+    for a, b, c, x in zip(s12, s13, s23, w):
+        merged[(a, b, c)] = merged.get((a, b, c), 0.0) + x
+    keys = list(merged)
+    return tuple(np.array([k[d] for k in keys]) for d in range(3)) + (
+        np.abs(np.array([merged[k] for k in keys])),)
+
+
+def _scale(Xq, Y2, Y3):
+    return off.pairset_sum(Xq, Y2, Y3, _merged_abs_terms())
+
+
+def _clusters(seed, n2, n3, nq, sep=4.0, rad=0.35):
+    rng = np.random.default_rng(seed)
+    Y2 = rng.normal(size=(n2, 3)) * rad + np.array([sep, 0.3, -0.2])
+    Y3 = rng.normal(size=(n3, 3)) * rad + np.array([0.5, sep, 0.4 * sep])
+    Xq = rng.normal(size=(nq, 3)) * rad
+    return Xq, Y2, Y3
+
+
+def _gpu(Xq, Y2, Y3, p, validate=True):
+    t = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (Xq, Y2, Y3)]
+    return api.farfield3(*t, p, validate=validate).cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def sets():
+    Xq, Y2, Y3 = _clusters(21, 300, 500, 1000)  # 1000 queries: 8 blocks, ragged last block
+    return Xq, Y2, Y3, _scale(Xq, Y2, Y3), off.pairset_sum(Xq, Y2, Y3)
+
+
+@pytest.mark.parametrize("p", range(7))
+def test_matches_oracle(sets, p):
+    Xq, Y2, Y3, scale, _ = sets
+    got = _gpu(Xq, Y2, Y3, p)
+    ref = off.farfield3(Xq, Y2, Y3, p)
+    dev = np.abs(got - ref) / scale
+    print(f"p={p}: max |gpu - oracle| / scale {dev.max():.2e}")
+    assert np.all(dev <= BAR)
+
+
+def test_error_falls_with_order(sets):
+    Xq, Y2, Y3, scale, exact = sets
+    err = [np.max(np.abs(_gpu(Xq, Y2, Y3, p) - exact) / np.abs(exact)) for p in range(7)]
+    print("max relative error vs the exact sum, p = 0..6:", ["%.1e" % e for e in err])
+    assert err[6] < 1e-3 * err[0]
+    assert all(err[p + 2] < err[p] for p in range(5))
+
+
+def test_tree_node_geometry():
+    """Three leaf-sized boxes of a uniform set (the paper's uniform workload):
+    axis-aligned boxes of side 1/16 at centre distances of 4-6 box sides."""
+    X = inputs.uniform_cube(60000, 1.0, 0.0, 33)
+    box = lambda lo: X[np.all((X >= lo) & (X < lo + 1 / 16), axis=1)]
+    Y2, Y3, Xq = box(np.array([0.5, 0.25, 0.25])), box(np.array([0.25, 0.5, 0.25])), \
+        box(np.array([0.25, 0.25, 0.25]))
+    scale = _scale(Xq, Y2, Y3)
+    for p in (0, 2, 4):
+        dev = np.abs(_gpu(Xq, Y2, Y3, p) - off.farfield3(Xq, Y2, Y3, p)) / scale
+        print(f"boxes ({len(Xq)}, {len(Y2)}, {len(Y3)}), p={p}: max dev / scale {dev.max():.2e}")
+        assert np.all(dev <= BAR)
+
+
+def test_single_points_are_exact():
+    rng = np.random.default_rng(4)
+    Xq = rng.normal(size=(130, 3))
+    y2, y3 = np.array([[3.0, 0.5, -0.2]]), np.array([[-0.4, 3.5, 0.3]])
+    exact = off.pairset_sum(Xq, y2, y3)
+    scale = _scale(Xq, y2, y3)
+    for p in (0, 3, 6):
+        assert np.all(np.abs(_gpu(Xq, y2, y3, p) - exact) <= BAR * scale)
+
+
+def test_full_size_sampled():
+    """2^20 queries against sources of 4096 points each, at the order the bench
+    times (p = 4); 256 sampled queries checked against the oracle."""
+    Xq, Y2, Y3 = _clusters(22, 4096, 4096, 1 << 20)
+    got = _gpu(Xq, Y2, Y3, 4)
+    idx = np.random.default_rng(1).choice(len(Xq), 256, replace=False)
+    ref = off.farfield3(Xq[idx], Y2, Y3, 4)
+    # scale: the monopole of the term magnitudes (n2 n3 sum_m |w_m| at the
+    # centres), within ~10 % of the pair-set sum at this separation, which
+    # would take 4096^2 pair evaluations per query
+    scale = off.farfield3(Xq[idx], Y2, Y3, 0, _merged_abs_terms())
+    dev = np.abs(got[idx] - ref) / scale
+    print("2^20 queries, p=4: max dev / scale", dev.max())
+    assert np.all(dev <= BAR) and np.all(np.isfinite(got))
+
+
+def test_deterministic(sets):
+    Xq, Y2, Y3, _, _ = sets
+    a, b = _gpu(Xq, Y2, Y3, 3), _gpu(Xq, Y2, Y3, 3)
+    assert np.array_equal(a, b)
+
+
+def test_empty_and_degenerate_inputs():
+    Xq, Y2, Y3 = _clusters(5, 10, 12, 7)
+    L = _lib.load()
+    ctx = api.default_context()
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    out = torch.full((7,), 5.0, dtype=torch.float64, device="cuda")
+    # empty source set: the double sum is zero
+    st = L.mbm_farfield3(ctx.handle, ctypes.c_void_p(d(Xq).data_ptr()), 7, None, 0,
+                         ctypes.c_void_p(d(Y3).data_ptr()), 12, 2, 1,
+                         ctypes.c_void_p(out.data_ptr()), None)
+    torch.cuda.synchronize()
+    assert st == 0 and torch.all(out == 0)
+    # no query points: nothing to do
+    assert L.mbm_farfield3(ctx.handle, None, 0, ctypes.c_void_p(d(Y2).data_ptr()), 10,
+                           ctypes.c_void_p(d(Y3).data_ptr()), 12, 2, 1, None, None) == 0
+    # order out of range
+    with pytest.raises(_lib.MbmError, match="order"):
+        _gpu(Xq, Y2, Y3, 7)
+    # coincident centres (the same set twice) and a query point at a centre
+    with pytest.raises(_lib.MbmError):
+        _gpu(Xq, Y2, Y2, 2)
+    # 8 dyadic points around a dyadic centre: their mean is exact in any order
+    c = np.array([4.0, 0.5, -0.25])
+    cube = c + 0.25 * np.array([[a, b, e] for a in (-1, 1) for b in (-1, 1) for e in (-1, 1)])
+    with pytest.raises(_lib.MbmError):
+        _gpu(np.vstack([Xq, c[None]]), cube, Y3, 2)
+    # the context stays usable
+    got = _gpu(Xq, Y2, Y3, 2)
+    assert np.all(np.abs(got - off.farfield3(Xq, Y2, Y3, 2)) <= BAR * _scale(Xq, Y2, Y3))
