@@ -88,22 +88,43 @@ constexpr MultiIndexTable make_table() {
 }
 __constant__ MultiIndexTable kAl = make_table();
 
-// The ten product terms as 2 s12, 2 s13, 2 s23 and w, grouped by s12 in the
-// order the query sweep visits them.
-__constant__ int kS23x2[kTerms] = {-5, -5, -3, -5, -3, -1, -5, -3, -1, 1};
-__constant__ double kW[kTerms] = {-0.375, 0.375, 0.375, 0.375, 0.25,
-                                  0.375,  -0.375, 0.375, 0.375, -0.375};
+// The ten product terms, grouped by s12 in the order the query sweep visits
+// them: (2 s12, 2 s13) = (1, -5), (-1, -3), (-1, -5), (-3, -1), (-3, -3),
+// (-3, -5), (-5, 1), (-5, -1), (-5, -3), (-5, -5); 2 s23 = -3 - 2 s12 - 2 s13
+// (the exponents of a term sum to -9/2). Weights 3/8 times the cubic's
+// coefficient (-1 on a^3, b^3, c^3; 1 on the a^2 b types), and 1/4 on
+// (-3, -3, -3) = 1 - (3/8) 2.
+__host__ __device__ constexpr int term_s23x2(int m) {
+    return m == 0 ? -5 : m == 1 ? -5 : m == 2 ? -3 : m == 3 ? -5 : m == 4 ? -3
+         : m == 5 ? -1 : m == 6 ? -5 : m == 7 ? -3 : m == 8 ? -1 : 1;
+}
+__host__ __device__ constexpr double term_w(int m) {
+    return m == 4 ? 0.25 : (m == 0 || m == 6 || m == 9) ? -0.375 : 0.375;
+}
 
-__device__ __forceinline__ double fact_d(int n) {
+// factorials and binomial coefficients up to 6 (every index of the sums is <= p)
+struct SmallTables {
+    double fact[kPMax + 1];
+    double inv[kPMax + 1];  // 1 / k (inv[0] unused)
+    double binom[kPMax + 1][kPMax + 1];
+};
+constexpr SmallTables make_small() {
+    SmallTables t{};
     double f = 1.0;
-    for (int i = 2; i <= n; ++i) f *= i;
-    return f;
+    for (int n = 0; n <= kPMax; ++n) {
+        if (n > 0) f *= n;
+        t.fact[n] = f;
+        t.inv[n] = n > 0 ? 1.0 / n : 0.0;
+        for (int k = 0; k <= kPMax; ++k) t.binom[n][k] = 0.0;
+        t.binom[n][0] = 1.0;
+        for (int k = 1; k <= n; ++k)
+            t.binom[n][k] = (n > 0 ? t.binom[n - 1][k - 1] : 0.0) + (k <= n - 1 ? t.binom[n - 1][k] : 0.0);
+    }
+    return t;
 }
-__device__ __forceinline__ double binom_d(int n, int k) {
-    double c = 1.0;
-    for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
-    return c;
-}
+__constant__ SmallTables kSmall = make_small();
+
+__device__ __forceinline__ double fact_d(int n) { return kSmall.fact[n]; }
 
 // ---------------------------------------------------------------- sums
 // part[set][b][3]: coordinate sums of block b's chunk of each source set.
@@ -168,7 +189,7 @@ ff_moments_kernel(const double* __restrict__ Y2, int64_t n2, const double* __res
                 double m = 1.0;
                 pw[t][d][0] = 1.0;
                 for (int k = 1; k <= p; ++k) {
-                    m = m * v / k;
+                    m = m * v * kSmall.inv[k];
                     pw[t][d][k] = m;
                 }
             }
@@ -192,6 +213,7 @@ __global__ void __launch_bounds__(kMomThreads)
 ff_finish_kernel(int64_t n2, int64_t n3, int nb, int p, const double* __restrict__ part,
                  const double* __restrict__ mpart, double* __restrict__ fin, int* __restrict__ flags) {
     __shared__ double w[3];
+    __shared__ double D[4][ff_n(kPMax)];
     const int na = ff_n(p);
     const int t = threadIdx.x;
     if (t < 6) {
@@ -212,48 +234,66 @@ ff_finish_kernel(int64_t n2, int64_t n3, int nb, int p, const double* __restrict
     __syncthreads();
     const double r2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
     if (t == 0 && !(r2 > 0.0)) atomicOr(flags, MBM_FLAG_COINCIDENT);
-    if (t < 4) {  // Taylor coefficients of (w.w)^s at w by the recurrence, then D = a! t
+    if (t < 4) {  // Taylor coefficients of (w.w)^s at w by the recurrence
         const int s2 = 1 - 2 * t;  // 2s = 1, -1, -3, -5
-        double* D = fin + kFinD + t * ff_n(kPMax);
-        const double r = sqrt(r2);
-        D[0] = pow(r, (double)s2);
+        const double r = sqrt(r2), ir2 = 1.0 / r2;
+        D[t][0] = pow(r, (double)s2);
         for (int q = 1; q < na; ++q) {
             const int i = kAl.a[q][0], j = kAl.a[q][1], l = kAl.a[q][2], k = i + j + l;
             double A = 0.0, B = 0.0;
-            if (i > 0) A += w[0] * D[ff_idx(i - 1, j, l)];
-            if (j > 0) A += w[1] * D[ff_idx(i, j - 1, l)];
-            if (l > 0) A += w[2] * D[ff_idx(i, j, l - 1)];
-            if (i > 1) B += D[ff_idx(i - 2, j, l)];
-            if (j > 1) B += D[ff_idx(i, j - 2, l)];
-            if (l > 1) B += D[ff_idx(i, j, l - 2)];
-            D[q] = ((s2 - 2 * k + 2) * A + (s2 - k + 2) * B) / (k * r2);
+            if (i > 0) A += w[0] * D[t][ff_idx(i - 1, j, l)];
+            if (j > 0) A += w[1] * D[t][ff_idx(i, j - 1, l)];
+            if (l > 0) A += w[2] * D[t][ff_idx(i, j, l - 1)];
+            if (i > 1) B += D[t][ff_idx(i - 2, j, l)];
+            if (j > 1) B += D[t][ff_idx(i, j - 2, l)];
+            if (l > 1) B += D[t][ff_idx(i, j, l - 2)];
+            D[t][q] = ((s2 - 2 * k + 2) * A + (s2 - k + 2) * B) * (kSmall.inv[k] * ir2);
         }
-        for (int q = 0; q < na; ++q)
-            D[q] *= fact_d(kAl.a[q][0]) * fact_d(kAl.a[q][1]) * fact_d(kAl.a[q][2]);
+    }
+    __syncthreads();
+    for (int q = t; q < 4 * na; q += kMomThreads) {  // D = a! t
+        const int sidx = q / na, a = q % na;
+        fin[kFinD + sidx * ff_n(kPMax) + a] =
+            D[sidx][a] * fact_d(kAl.a[a][0]) * fact_d(kAl.a[a][1]) * fact_d(kAl.a[a][2]);
     }
 }
 
 // ---------------------------------------------------------------- K
 // One block per row a12; thread columns a13. K[m][row offset + col] in FP32.
+// The moments, the g23 derivatives and the small tables are staged in shared
+// memory first: the threads of a warp index them at different places.
 __global__ void __launch_bounds__(kMomThreads)
 ff_k_kernel(int p, const double* __restrict__ fin, float* __restrict__ K) {
+    __shared__ double M2[ff_n(kPMax)], M3[ff_n(kPMax)], D23[4][ff_n(kPMax)];
+    __shared__ int binom[kPMax + 1][kPMax + 1];  // C(n, k) <= 20: products of six fit in int
+    __shared__ double fact[kPMax + 1];
+    __shared__ unsigned char al[ff_n(kPMax)][3];
+    const int na = ff_n(p);
+    for (int q = threadIdx.x; q < na; q += kMomThreads) {
+        M2[q] = fin[kFinM2 + q];
+        M3[q] = fin[kFinM3 + q];
+        for (int d = 0; d < 3; ++d) al[q][d] = kAl.a[q][d];
+        for (int sidx = 0; sidx < 4; ++sidx) D23[sidx][q] = fin[kFinD + sidx * ff_n(kPMax) + q];
+    }
+    for (int q = threadIdx.x; q < (kPMax + 1) * (kPMax + 1); q += kMomThreads)
+        binom[q / (kPMax + 1)][q % (kPMax + 1)] = (int)kSmall.binom[q / (kPMax + 1)][q % (kPMax + 1)];
+    if (threadIdx.x <= kPMax) fact[threadIdx.x] = kSmall.fact[threadIdx.x];
+    __syncthreads();
     const int r = blockIdx.x;  // a12 index
-    const int i12 = kAl.a[r][0], j12 = kAl.a[r][1], l12 = kAl.a[r][2], d12 = i12 + j12 + l12;
+    const int i12 = al[r][0], j12 = al[r][1], l12 = al[r][2], d12 = i12 + j12 + l12;
     const int L = ff_n(p - d12);
     int off = 0;
     for (int d = 0; d < d12; ++d) off += (d + 1) * (d + 2) / 2 * pad4(ff_n(p - d));
     off += (r - ff_n(d12 - 1)) * pad4(L);
     const int stride = k_stride(p);
-    const double* M2 = fin + kFinM2;
-    const double* M3 = fin + kFinM3;
     for (int c = threadIdx.x; c < pad4(L); c += kMomThreads) {
-        double acc[kTerms];
-        for (int m = 0; m < kTerms; ++m) acc[m] = 0.0;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};  // by the power of g23: 2s = 1, -1, -3, -5
+        double f = 0.0;
         if (c < L) {
-            const int i13 = kAl.a[c][0], j13 = kAl.a[c][1], l13 = kAl.a[c][2];
+            const int i13 = al[c][0], j13 = al[c][1], l13 = al[c][2];
             const int d13 = i13 + j13 + l13;
             for (int q = 0; q < ff_n(p - d12 - d13); ++q) {  // a23
-                const int i23 = kAl.a[q][0], j23 = kAl.a[q][1], l23 = kAl.a[q][2];
+                const int i23 = al[q][0], j23 = al[q][1], l23 = al[q][2];
                 double S = 0.0;
                 for (int ib = 0; ib <= i23; ++ib)
                     for (int jb = 0; jb <= j23; ++jb)
@@ -261,21 +301,18 @@ ff_k_kernel(int p, const double* __restrict__ fin, float* __restrict__ K) {
                             const int gi = i12 + ib, gj = j12 + jb, gl = l12 + lb;  // a12 + b
                             const int hi = i13 + i23 - ib, hj = j13 + j23 - jb,
                                       hl = l13 + l23 - lb;  // a13 + a23 - b
-                            const double cb = binom_d(gi, i12) * binom_d(gj, j12) * binom_d(gl, l12) *
-                                              binom_d(hi, i13) * binom_d(hj, j13) * binom_d(hl, l13);
-                            const double v = cb * M2[ff_idx(gi, gj, gl)] * M3[ff_idx(hi, hj, hl)];
-                            S += ((ib + jb + lb) & 1) ? -v : v;
+                            int cb = binom[gi][i12] * binom[gj][j12] * binom[gl][l12] *
+                                     binom[hi][i13] * binom[hj][j13] * binom[hl][l13];
+                            if ((ib + jb + lb) & 1) cb = -cb;
+                            S = fma((double)cb * M2[ff_idx(gi, gj, gl)], M3[ff_idx(hi, hj, hl)], S);
                         }
-                for (int m = 0; m < kTerms; ++m) {
-                    const int sidx = (1 - kS23x2[m]) / 2;  // 2s = 1, -1, -3, -5 -> 0..3
-                    acc[m] += S * fin[kFinD + sidx * ff_n(kPMax) + q];
-                }
+                for (int sidx = 0; sidx < 4; ++sidx) acc[sidx] += S * D23[sidx][q];
             }
-            const double f = fact_d(i12) * fact_d(j12) * fact_d(l12) * fact_d(i13) * fact_d(j13) *
-                             fact_d(l13);
-            for (int m = 0; m < kTerms; ++m) acc[m] *= kW[m] * f;
+            f = fact[i12] * fact[j12] * fact[l12] * fact[i13] * fact[j13] * fact[l13];
         }
-        for (int m = 0; m < kTerms; ++m) K[m * stride + off + c] = (float)acc[m];
+#pragma unroll
+        for (int m = 0; m < kTerms; ++m)
+            K[m * stride + off + c] = (float)(acc[(1 - term_s23x2(m)) / 2] * term_w(m) * f);
     }
 }
 
@@ -347,26 +384,25 @@ ff_eval_kernel(const double* __restrict__ Xq, int64_t nq, const float* __restric
     const double c3x = fin[kFinC + 3], c3y = fin[kFinC + 4], c3z = fin[kFinC + 5];
     for (int64_t i = (int64_t)blockIdx.x * kEvalThreads + threadIdx.x; i < nq;
          i += (int64_t)gridDim.x * kEvalThreads) {
+        // x - c in FP64 (the difference of two far-apart points), rounded once
         const double x = Xq[3 * i], y = Xq[3 * i + 1], z = Xq[3 * i + 2];
-        const double ux = x - c2x, uy = y - c2y, uz = z - c2z;
-        const double vx = x - c3x, vy = y - c3y, vz = z - c3z;
-        const double ru2 = ux * ux + uy * uy + uz * uz, rv2 = vx * vx + vy * vy + vz * vz;
-        if (!(ru2 > 0.0) || !(rv2 > 0.0) || !isfinite(ru2 + rv2)) {
+        const float fux = (float)(x - c2x), fuy = (float)(y - c2y), fuz = (float)(z - c2z);
+        const float fvx = (float)(x - c3x), fvy = (float)(y - c3y), fvz = (float)(z - c3z);
+        const float ru2 = fmaf(fux, fux, fmaf(fuy, fuy, fuz * fuz));
+        const float rv2 = fmaf(fvx, fvx, fmaf(fvy, fvy, fvz * fvz));
+        if (!(ru2 > 0.f) || !(rv2 > 0.f) || !isfinite(ru2 + rv2)) {
             atomicOr(flags, isfinite(ru2 + rv2) ? MBM_FLAG_COINCIDENT : MBM_FLAG_NONFINITE);
             out[i] = __longlong_as_double(0x7ff8000000000000ll);
             continue;
         }
-        const double riu = rsqrt(ru2), riv = rsqrt(rv2);
-        const float fux = (float)ux, fuy = (float)uy, fuz = (float)uz;
-        const float fvx = (float)vx, fvy = (float)vy, fvz = (float)vz;
-        const float u2i = (float)(riu * riu), v2i = (float)(riv * riv);
-        const float ru = (float)(ru2 * riu), rv = (float)(rv2 * riv);  // |u|, |v|
-        const float iu = (float)riu, iv = (float)riv;
-        const float iu3 = (float)(riu * riu * riu), iv3 = (float)(riv * riv * riv);
-        const float iu5 = (float)(riu * riu * riu * riu * riu), iv5 = (float)(riv * riv * riv * riv * riv);
+        const float iu = rsqrtf(ru2), iv = rsqrtf(rv2);
+        const float u2i = iu * iu, v2i = iv * iv;
+        const float ru = ru2 * iu, rv = rv2 * iv;  // |u|, |v|
+        const float iu3 = iu * u2i, iv3 = iv * v2i;
+        const float iu5 = iu3 * u2i, iv5 = iv3 * v2i;
         float tu[ff_n(P)], tv[ff_n(P)];
         double acc = 0.0;
-        // terms in the order of kS23x2 / kW: (2 s12, 2 s13)
+        // terms in the order of term_s23x2 / term_w: (2 s12, 2 s13)
         taylor<P, 1>(fux, fuy, fuz, u2i, ru, tu);
         taylor<P, -5>(fvx, fvy, fvz, v2i, iv5, tv);
         acc += contract<P>(tu, tv, Ks + 0 * kStride);
@@ -430,11 +466,12 @@ cudaError_t launch_eval_p(int p, const double* Xq, int64_t nq, const float* K, c
     }
 }
 
-// blocks per source set for the sums and moments
+// blocks per source set for the sums and moments: chunks of at least 128
+// points, at most four blocks per SM
 int source_blocks(int64_t n2, int64_t n3, int num_sms) {
     const int64_t n = n2 > n3 ? n2 : n3;
-    int64_t nb = (n + 4095) / 4096;
-    if (nb > num_sms) nb = num_sms;
+    int64_t nb = (n + kMomThreads - 1) / kMomThreads;
+    if (nb > 4 * (int64_t)num_sms) nb = 4 * (int64_t)num_sms;
     return nb < 1 ? 1 : (int)nb;
 }
 
@@ -449,9 +486,10 @@ size_t mbm_farfield3_scratch_bytes(int64_t n2, int64_t n3, int num_sms) {
 }
 
 // Enqueue the whole expansion; scratch must hold mbm_farfield3_scratch_bytes.
-cudaError_t launch_farfield3(const double* Xq, int64_t nq, const double* Y2, int64_t n2,
-                             const double* Y3, int64_t n3, int p, double* out, void* scratch,
-                             int* flags, int num_sms, cudaStream_t s) {
+// With ctx, its timing events bracket the query sweep.
+cudaError_t launch_farfield3(mbm_ctx* ctx, const double* Xq, int64_t nq, const double* Y2,
+                             int64_t n2, const double* Y3, int64_t n3, int p, double* out,
+                             void* scratch, int* flags, int num_sms, cudaStream_t s) {
     const int nb = source_blocks(n2, n3, num_sms);
     char* b = static_cast<char*>(scratch);
     auto* part = reinterpret_cast<double*>(b);
@@ -470,7 +508,10 @@ cudaError_t launch_farfield3(const double* Xq, int64_t nq, const double* Y2, int
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ff_k_kernel<<<ff_n(p), kMomThreads, 0, s>>>(p, fin, K);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_eval_p(p, Xq, nq, K, fin, out, flags, num_sms, s);
+    if (ctx) mbm_time_begin(ctx, s);
+    e = launch_eval_p(p, Xq, nq, K, fin, out, flags, num_sms, s);
+    if (ctx) mbm_time_end(ctx, s);
+    return e;
 }
 
 extern "C" mbm_status mbm_farfield3(mbm_ctx* ctx, const double* Xq_dev, int64_t nq,
@@ -494,10 +535,8 @@ extern "C" mbm_status mbm_farfield3(mbm_ctx* ctx, const double* Xq_dev, int64_t 
     }
     MBM_TRY(mbm_scratch_reserve(ctx, mbm_farfield3_scratch_bytes(n2, n3, ctx->num_sms)));
     MBM_CUDA_TRY(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), s));
-    mbm_time_begin(ctx, s);
-    MBM_CUDA_TRY(launch_farfield3(Xq_dev, nq, Y2_dev, n2, Y3_dev, n3, p, out_dev, ctx->scratch,
-                                  ctx->d_flags, ctx->num_sms, s));
-    mbm_time_end(ctx, s);
+    MBM_CUDA_TRY(launch_farfield3(ctx, Xq_dev, nq, Y2_dev, n2, Y3_dev, n3, p, out_dev,
+                                  ctx->scratch, ctx->d_flags, ctx->num_sms, s));
     if (validate) return mbm_check_flags(ctx, s);
     return MBM_OK;
 }

