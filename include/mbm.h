@@ -189,8 +189,7 @@ mbm_status mbm_potential_sampled(mbm_ctx* ctx, const double* X_dev, int64_t N,
  * (|y - c| small against the distances between x, c2 and c3).
  *   out_dev: caller-owned FP64[nq] on the device.
  *   p: 0..6. Moments and the source-dependent coefficients are FP64; each
- *   query point is evaluated in FP32 arithmetic with an FP64 sum over the
- *   ten product terms.
+ *   query point is evaluated in FP32 arithmetic from FP64 differences x - c.
  *   n2 == 0 or n3 == 0: the double sum is empty, out = 0.
  *   The sets are taken as given: the caller keeps x out of P2 and P3 (as for
  *   distinct tree nodes); P2 and P3 may share points, but not a centre.

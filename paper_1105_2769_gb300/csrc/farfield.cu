@@ -27,8 +27,9 @@
 // quadruple sum with a = a12 + a13 + a23 regrouped: K holds everything that
 // does not depend on x, so it is formed once per call (FP64), and a query
 // point costs the Taylor coefficients of four powers at x - c2 and at x - c3
-// and one contraction with K per product term (FP32 arithmetic, K in shared
-// memory, FP64 sum over the ten terms) instead of the O(p^6) sum per point.
+// and one contraction with K per product term (FP32 arithmetic after the
+// FP64 differences x - c, K in shared memory) instead of the O(p^6) sum per
+// point.
 //
 // Taylor coefficients come from a recurrence: f = (v.v)^s satisfies
 // (v.v) grad f = 2 s v f; the coefficient of t^a on both sides at v0 + t gives
@@ -401,7 +402,7 @@ ff_eval_kernel(const double* __restrict__ Xq, int64_t nq, const float* __restric
         const float iu3 = iu * u2i, iv3 = iv * v2i;
         const float iu5 = iu3 * u2i, iv5 = iv3 * v2i;
         float tu[ff_n(P)], tv[ff_n(P)];
-        double acc = 0.0;
+        float acc = 0.f;  // the terms' own FP32 roundings set the error scale
         // terms in the order of term_s23x2 / term_w: (2 s12, 2 s13)
         taylor<P, 1>(fux, fuy, fuz, u2i, ru, tu);
         taylor<P, -5>(fvx, fvy, fvz, v2i, iv5, tv);
@@ -427,7 +428,7 @@ ff_eval_kernel(const double* __restrict__ Xq, int64_t nq, const float* __restric
         acc += contract<P>(tu, tv, Ks + 8 * kStride);
         taylor<P, -5>(fvx, fvy, fvz, v2i, iv5, tv);
         acc += contract<P>(tu, tv, Ks + 9 * kStride);
-        out[i] = acc;
+        out[i] = (double)acc;
     }
 }
 

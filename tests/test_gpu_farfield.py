@@ -3,8 +3,8 @@ far-field oracle (§3.2, Eq. truncated_three_body_farfield_expansion).
 
 Bar (written here): the GPU evaluates each query point in FP32 arithmetic
 (Taylor recurrences of four powers at x - c2 and at x - c3, contractions of
-at most 84 x 84 coefficients) with FP64 moments and an FP64 sum over the ten
-product terms. Each term carries a few hundred FP32 roundings relative to its
+at most 84 x 84 coefficients, the sum over the ten product terms) from FP64
+moments and FP64 differences x - c. Each term carries a few hundred FP32 roundings relative to its
 own size, and the terms cancel in phi, so the error is measured against the
 magnitudes of the ten product terms summed over the source pairs, scale(x) =
 sum_{y2, y3} sum_m |w_m| a^s12 b^s13 c^s23 (the oracle's pair-set sum with
