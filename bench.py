@@ -492,12 +492,13 @@ def farfield_flops_per_query(p):
     return 14 * taylor + 10 * contract
 
 
-def run_farfield_only(args):
-    """The three-body far-field expansion (mbm_farfield3) at orders 0..6 on
-    2^20 query points against two source clusters of 4 096 points each
-    (Gaussian, radius 0.35, centre distances 4-6.4: the separations of pruned
-    node triples), timed with CUDA events on the launching stream; accuracy of
-    64 sampled queries against the exact double sum (FP64 oracle)."""
+def bench_farfield(orders, n_exact):
+    """The three-body far-field expansion (mbm_farfield3) on 2^20 query points
+    against two source clusters of 4 096 points each (Gaussian, radius 0.35,
+    centre distances 4-6.4: the separations of pruned node triples): the
+    whole call and the query sweep alone timed with CUDA events on the
+    launching stream; accuracy of n_exact sampled queries against the exact
+    double sum (FP64 oracle) and against the oracle's expansion."""
     import numpy as np
     import torch
 
@@ -511,14 +512,14 @@ def run_farfield_only(args):
     Y3 = rng.normal(size=(n_src, 3)) * 0.35 + np.array([0.5, 4.0, 1.6])
     Xq = rng.normal(size=(nq, 3)) * 0.35
     d = [torch.from_numpy(a).to(dev) for a in (Xq, Y2, Y3)]
-    idx = rng.choice(nq, 64, replace=False)
+    idx = rng.choice(nq, n_exact, replace=False)
     t0 = time.perf_counter()
     exact = off.pairset_sum(Xq[idx], Y2, Y3)
     t_exact = time.perf_counter() - t0
     peak = fp32_peak_tflops(torch, dev)
     ctx = api.default_context(0)
     rows = []
-    for p in range(7):
+    for p in orders:
         out = api.farfield3(*d, p)
         for _ in range(3):
             api.farfield3(*d, p)
@@ -550,12 +551,18 @@ def run_farfield_only(args):
                                   "unit": "TFLOP/s", "frac": achieved / peak,
                                   "kernel": f"ff_eval_kernel<{p}>",
                                   "flops_per_query": fl, "traffic": None}})
-        print(json.dumps({"progress": rows[-1]}), flush=True)
-    pair_rate = len(idx) * n_src * n_src / t_exact
-    print(json.dumps({"report": "farfield", "queries": nq, "sources": [n_src, n_src],
-                      "workload": "Gaussian clusters radius 0.35 at centre distances 4-6.4, seed 22",
-                      "exact_pairs_per_s_cpu_oracle": pair_rate,
-                      "exact_cores": oracle.max_threads(), "rows": rows}))
+    return {"queries": nq, "sources": [n_src, n_src], "sampled_queries": n_exact,
+            "workload": "Gaussian clusters radius 0.35 at centre distances 4-6.4, seed 22",
+            "exact_pairs_per_s_cpu_oracle": n_exact * n_src * n_src / t_exact,
+            "exact_cores": oracle.max_threads(), "rows": rows}
+
+
+def run_farfield_only(args):
+    """bench_farfield at every order 0..6, 64 sampled queries."""
+    rep = bench_farfield(range(7), 64)
+    for r in rep["rows"]:
+        print(json.dumps({"progress": r}), flush=True)
+    print(json.dumps({"report": "farfield", **rep}))
     return 0
 
 
@@ -761,6 +768,7 @@ def main():
         line["fp64_exhaustive"] = fp64
         line["tree"] = bench_tree(api, inputs, torch, dev, fp64["triples_per_s"], np)
         line["forces"] = bench_forces(api, inputs, torch, dev)
+        line["farfield"] = bench_farfield((2, 4), 16)
         line["serving"] = bench_serving(api, inputs, np)
         # the same mix at an offered load the server keeps up with
         line["serving_at_100_req_s"] = bench_serving(api, inputs, np, rate=100.0)

@@ -38,8 +38,8 @@
 // Kernels, in stream order: coordinate sums per block of each source set;
 // moments per block about the centre; one block finishing the moments, the
 // centres and the Taylor coefficients of the four powers at c2 - c3; K, one
-// block per row a12; the query sweep. Every reduction runs in a fixed order,
-// so results do not depend on scheduling.
+// warp per coefficient (a12, a13); the query sweep. Every reduction runs in a
+// fixed order, so results do not depend on scheduling.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -235,23 +235,27 @@ ff_finish_kernel(int64_t n2, int64_t n3, int nb, int p, const double* __restrict
     __syncthreads();
     const double r2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
     if (t == 0 && !(r2 > 0.0)) atomicOr(flags, MBM_FLAG_COINCIDENT);
-    if (t < 4) {  // Taylor coefficients of (w.w)^s at w by the recurrence
-        const int s2 = 1 - 2 * t;  // 2s = 1, -1, -3, -5
-        const double r = sqrt(r2), ir2 = 1.0 / r2;
-        D[t][0] = pow(r, (double)s2);
-        for (int q = 1; q < na; ++q) {
-            const int i = kAl.a[q][0], j = kAl.a[q][1], l = kAl.a[q][2], k = i + j + l;
-            double A = 0.0, B = 0.0;
-            if (i > 0) A += w[0] * D[t][ff_idx(i - 1, j, l)];
-            if (j > 0) A += w[1] * D[t][ff_idx(i, j - 1, l)];
-            if (l > 0) A += w[2] * D[t][ff_idx(i, j, l - 1)];
-            if (i > 1) B += D[t][ff_idx(i - 2, j, l)];
-            if (j > 1) B += D[t][ff_idx(i, j - 2, l)];
-            if (l > 1) B += D[t][ff_idx(i, j, l - 2)];
-            D[t][q] = ((s2 - 2 * k + 2) * A + (s2 - k + 2) * B) * (kSmall.inv[k] * ir2);
-        }
-    }
+    // Taylor coefficients of (w.w)^s at w by the recurrence, one degree level
+    // at a time (every coefficient of a level depends only on lower levels)
+    const double ir2 = 1.0 / r2;
+    if (t < 4) D[t][0] = pow(sqrt(r2), (double)(1 - 2 * t));  // 2s = 1, -1, -3, -5
     __syncthreads();
+    for (int k = 1; k <= p; ++k) {
+        const int lo = ff_n(k - 1), cnt = ff_n(k) - lo;
+        for (int q = t; q < 4 * cnt; q += kMomThreads) {
+            const int sidx = q / cnt, a = lo + q % cnt, s2 = 1 - 2 * sidx;
+            const int i = kAl.a[a][0], j = kAl.a[a][1], l = kAl.a[a][2];
+            double A = 0.0, B = 0.0;
+            if (i > 0) A += w[0] * D[sidx][ff_idx(i - 1, j, l)];
+            if (j > 0) A += w[1] * D[sidx][ff_idx(i, j - 1, l)];
+            if (l > 0) A += w[2] * D[sidx][ff_idx(i, j, l - 1)];
+            if (i > 1) B += D[sidx][ff_idx(i - 2, j, l)];
+            if (j > 1) B += D[sidx][ff_idx(i, j - 2, l)];
+            if (l > 1) B += D[sidx][ff_idx(i, j, l - 2)];
+            D[sidx][a] = ((s2 - 2 * k + 2) * A + (s2 - k + 2) * B) * (kSmall.inv[k] * ir2);
+        }
+        __syncthreads();
+    }
     for (int q = t; q < 4 * na; q += kMomThreads) {  // D = a! t
         const int sidx = q / na, a = q % na;
         fin[kFinD + sidx * ff_n(kPMax) + a] =
@@ -260,57 +264,69 @@ ff_finish_kernel(int64_t n2, int64_t n3, int nb, int p, const double* __restrict
 }
 
 // ---------------------------------------------------------------- K
-// One block per row a12; thread columns a13. K[m][row offset + col] in FP32.
-// The moments, the g23 derivatives and the small tables are staged in shared
-// memory first: the threads of a warp index them at different places.
-__global__ void __launch_bounds__(kMomThreads)
+// Grid (row a12, column group): warp w of a block owns column a13 =
+// 4 blockIdx.y + w of row a12; its lanes take the a23 terms of the sum and
+// a fixed butterfly adds them, so results do not depend on scheduling.
+// K[m][row offset + col] in FP32. The moments, the g23 derivatives and the
+// small tables are staged in shared memory first: the lanes of a warp index
+// them at different places.
+constexpr int kKWarps = 4;
+
+__global__ void __launch_bounds__(kKWarps * 32)
 ff_k_kernel(int p, const double* __restrict__ fin, float* __restrict__ K) {
     __shared__ double M2[ff_n(kPMax)], M3[ff_n(kPMax)], D23[4][ff_n(kPMax)];
     __shared__ int binom[kPMax + 1][kPMax + 1];  // C(n, k) <= 20: products of six fit in int
     __shared__ double fact[kPMax + 1];
     __shared__ unsigned char al[ff_n(kPMax)][3];
     const int na = ff_n(p);
-    for (int q = threadIdx.x; q < na; q += kMomThreads) {
+    for (int q = threadIdx.x; q < na; q += kKWarps * 32) {
         M2[q] = fin[kFinM2 + q];
         M3[q] = fin[kFinM3 + q];
         for (int d = 0; d < 3; ++d) al[q][d] = kAl.a[q][d];
         for (int sidx = 0; sidx < 4; ++sidx) D23[sidx][q] = fin[kFinD + sidx * ff_n(kPMax) + q];
     }
-    for (int q = threadIdx.x; q < (kPMax + 1) * (kPMax + 1); q += kMomThreads)
+    for (int q = threadIdx.x; q < (kPMax + 1) * (kPMax + 1); q += kKWarps * 32)
         binom[q / (kPMax + 1)][q % (kPMax + 1)] = (int)kSmall.binom[q / (kPMax + 1)][q % (kPMax + 1)];
     if (threadIdx.x <= kPMax) fact[threadIdx.x] = kSmall.fact[threadIdx.x];
     __syncthreads();
     const int r = blockIdx.x;  // a12 index
     const int i12 = al[r][0], j12 = al[r][1], l12 = al[r][2], d12 = i12 + j12 + l12;
     const int L = ff_n(p - d12);
+    const int c = blockIdx.y * kKWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= pad4(L)) return;
     int off = 0;
     for (int d = 0; d < d12; ++d) off += (d + 1) * (d + 2) / 2 * pad4(ff_n(p - d));
     off += (r - ff_n(d12 - 1)) * pad4(L);
     const int stride = k_stride(p);
-    for (int c = threadIdx.x; c < pad4(L); c += kMomThreads) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};  // by the power of g23: 2s = 1, -1, -3, -5
-        double f = 0.0;
-        if (c < L) {
-            const int i13 = al[c][0], j13 = al[c][1], l13 = al[c][2];
-            const int d13 = i13 + j13 + l13;
-            for (int q = 0; q < ff_n(p - d12 - d13); ++q) {  // a23
-                const int i23 = al[q][0], j23 = al[q][1], l23 = al[q][2];
-                double S = 0.0;
-                for (int ib = 0; ib <= i23; ++ib)
-                    for (int jb = 0; jb <= j23; ++jb)
-                        for (int lb = 0; lb <= l23; ++lb) {
-                            const int gi = i12 + ib, gj = j12 + jb, gl = l12 + lb;  // a12 + b
-                            const int hi = i13 + i23 - ib, hj = j13 + j23 - jb,
-                                      hl = l13 + l23 - lb;  // a13 + a23 - b
-                            int cb = binom[gi][i12] * binom[gj][j12] * binom[gl][l12] *
-                                     binom[hi][i13] * binom[hj][j13] * binom[hl][l13];
-                            if ((ib + jb + lb) & 1) cb = -cb;
-                            S = fma((double)cb * M2[ff_idx(gi, gj, gl)], M3[ff_idx(hi, hj, hl)], S);
-                        }
-                for (int sidx = 0; sidx < 4; ++sidx) acc[sidx] += S * D23[sidx][q];
-            }
-            f = fact[i12] * fact[j12] * fact[l12] * fact[i13] * fact[j13] * fact[l13];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};  // by the power of g23: 2s = 1, -1, -3, -5
+    double f = 0.0;
+    if (c < L) {
+        const int i13 = al[c][0], j13 = al[c][1], l13 = al[c][2];
+        const int d13 = i13 + j13 + l13;
+        for (int q = lane; q < ff_n(p - d12 - d13); q += 32) {  // a23
+            const int i23 = al[q][0], j23 = al[q][1], l23 = al[q][2];
+            double S = 0.0;
+            for (int ib = 0; ib <= i23; ++ib)
+                for (int jb = 0; jb <= j23; ++jb)
+                    for (int lb = 0; lb <= l23; ++lb) {
+                        const int gi = i12 + ib, gj = j12 + jb, gl = l12 + lb;  // a12 + b
+                        const int hi = i13 + i23 - ib, hj = j13 + j23 - jb,
+                                  hl = l13 + l23 - lb;  // a13 + a23 - b
+                        int cb = binom[gi][i12] * binom[gj][j12] * binom[gl][l12] *
+                                 binom[hi][i13] * binom[hj][j13] * binom[hl][l13];
+                        if ((ib + jb + lb) & 1) cb = -cb;
+                        S = fma((double)cb * M2[ff_idx(gi, gj, gl)], M3[ff_idx(hi, hj, hl)], S);
+                    }
+#pragma unroll
+            for (int sidx = 0; sidx < 4; ++sidx) acc[sidx] += S * D23[sidx][q];
         }
+        f = fact[i12] * fact[j12] * fact[l12] * fact[i13] * fact[j13] * fact[l13];
+    }
+#pragma unroll
+    for (int sidx = 0; sidx < 4; ++sidx)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[sidx] += __shfl_xor_sync(0xffffffffu, acc[sidx], o);
+    if (lane == 0) {
 #pragma unroll
         for (int m = 0; m < kTerms; ++m)
             K[m * stride + off + c] = (float)(acc[(1 - term_s23x2(m)) / 2] * term_w(m) * f);
@@ -507,7 +523,7 @@ cudaError_t launch_farfield3(mbm_ctx* ctx, const double* Xq, int64_t nq, const d
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ff_finish_kernel<<<1, kMomThreads, 0, s>>>(n2, n3, nb, p, part, mpart, fin, flags);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ff_k_kernel<<<ff_n(p), kMomThreads, 0, s>>>(p, fin, K);
+    ff_k_kernel<<<dim3(ff_n(p), pad4(ff_n(p)) / kKWarps), kKWarps * 32, 0, s>>>(p, fin, K);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ctx) mbm_time_begin(ctx, s);
     e = launch_eval_p(p, Xq, nq, K, fin, out, flags, num_sms, s);
