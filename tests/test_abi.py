@@ -75,3 +75,6 @@ def test_null_and_bad_arguments_rejected_on_host(lib):
     assert st in (-1, -7)
     assert lib.mbm_ctx_destroy(None) == 0
     assert _lib.STATUS_NAMES[-1] == "MBM_EINVAL"
+    # far-field expansion: NULL context, then order checks, before any CUDA call
+    assert lib.mbm_farfield3(None, None, 4, None, 3, None, 3, 2, 1, None, None) == -1
+    assert b"ctx" in lib.mbm_last_error()
