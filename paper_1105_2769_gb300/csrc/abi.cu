@@ -39,7 +39,7 @@ extern "C" void mbm_config_default(mbm_config* cfg) {
     cfg->seed = 0x5eed5eedULL;
     cfg->mc_rule = 0;
     cfg->validate = 1;
-    cfg->seed_levels = 7;
+    cfg->seed_levels = 8;
     cfg->tuple_counts = nullptr;
 }
 

@@ -1770,7 +1770,7 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
                              cudaStream_t s, mbm_tree** out) {
     if (N < 3) return mbm_fail(MBM_EINVAL, "tree needs N >= 3");
     if (cfg.leaf_size < 2 || cfg.leaf_size > kTile) return mbm_fail(MBM_EINVAL, "leaf_size must be in [2, 32]");
-    if (cfg.seed_levels < 0 || cfg.seed_levels > 7) return mbm_fail(MBM_EINVAL, "seed_levels must be in [0, 7]");
+    if (cfg.seed_levels < 0 || cfg.seed_levels > 8) return mbm_fail(MBM_EINVAL, "seed_levels must be in [0, 8]");
     const int depth = tree_depth(N, cfg.leaf_size);
     const int64_t n_nodes = ((int64_t)2 << depth) - 1, n_leaves = (int64_t)1 << depth;
     if (n_nodes >= (1 << 24)) return mbm_fail(MBM_EINVAL, "tree too large (node ids are 24-bit)");

@@ -50,7 +50,7 @@ def test_version_and_defaults(lib):
     assert b"sm_103a" in lib.mbm_version()
     c = _lib.default_config()
     assert c.leaf_size == 32 and c.m_limit == 256 and c.zeta == 32.0 and c.validate == 1
-    assert c.seed_levels == 7 and not c.tuple_counts
+    assert c.seed_levels == 8 and not c.tuple_counts
 
 
 def test_ctx_create_without_gpu_fails_cleanly(lib):
