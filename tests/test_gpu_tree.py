@@ -153,7 +153,7 @@ def test_bad_arguments(gmm):
     with pytest.raises(_lib.MbmError):
         api.potential(Xd, eps=0.1, mode="tree", config=api.tree_config(leaf_size=64))
     with pytest.raises(_lib.MbmError):
-        api.potential(Xd, eps=0.1, mode="tree", config=api.tree_config(seed_levels=8))
+        api.potential(Xd, eps=0.1, mode="tree", config=api.tree_config(seed_levels=9))
 
 
 def test_hybrid_rule(gmm):
