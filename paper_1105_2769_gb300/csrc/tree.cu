@@ -1810,7 +1810,7 @@ static mbm_status build_tree(mbm_ctx* ctx, const double* X, int64_t N, const mbm
     t->pphil = cv.take<double>(N);
     t->weak = cv.take<int>((size_t)n_nodes * 32);
 
-    // Temporary scratch: box partials, keys/indices (double-buffered), CUB temp, seed sums.
+    // Temporary scratch: box partials, keys/indices (double-buffered), sort temp, seed sums.
     const int nb = 256;
     const size_t sort_tmp_bytes = mbm_sort_temp_bytes(N);
     const int sd = std::max(0, depth - cfg.seed_levels);
