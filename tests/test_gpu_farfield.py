@@ -118,6 +118,18 @@ def test_full_size_sampled():
     assert np.all(dev <= BAR) and np.all(np.isfinite(got))
 
 
+def test_large_source_sets():
+    """Source sets of 200 000 and 150 000 points: the moments run in 608 blocks
+    of several 128-point stages each (and unequal chunks for the two sets)."""
+    Xq, Y2, Y3 = _clusters(23, 200_000, 150_000, 300, sep=6.0, rad=0.5)
+    got = _gpu(Xq, Y2, Y3, 3)
+    ref = off.farfield3(Xq, Y2, Y3, 3)
+    scale = off.farfield3(Xq, Y2, Y3, 0, _merged_abs_terms())  # monopole of |terms|
+    dev = np.abs(got - ref) / scale
+    print("sources 200 000 / 150 000, p=3: max dev / scale", dev.max())
+    assert np.all(dev <= BAR)
+
+
 def test_deterministic(sets):
     Xq, Y2, Y3, _, _ = sets
     a, b = _gpu(Xq, Y2, Y3, 3), _gpu(Xq, Y2, Y3, 3)
