@@ -67,7 +67,8 @@ typedef struct {
     uint64_t seed;       /* Philox-4x32-10 key for Monte Carlo draws */
     int32_t mc_rule;     /* 0 = relative stop test with T_i on both terms, 1 = as printed */
     int32_t validate;    /* 1: synchronise and report non-finite/coincident input */
-    int32_t seed_levels; /* Phi^l seed node = ancestor this many levels above a leaf, 0-8 (default 8) */
+    int32_t seed_levels; /* Phi^l seed node = ancestor this many levels above a leaf, 0-8
+                            (default 8); the force criterion's A^l seed uses at most 6 */
     int32_t reserved0;
     int64_t* tuple_counts; /* optional device int64[N]: point triples credited to each
                               particle by prunes and base cases (validation; NULL = off) */

@@ -1522,9 +1522,18 @@ seed_scale_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, 
 // gradient alone. Masked pairs have zero terms and contribute exactly 0.
 constexpr int kForceWarps = 4;
 constexpr int kForceCols = 8;
+// Largest seed level of the force criterion's A^l: the seed pass costs the
+// seed node's size squared per particle and, for gradients, outweighs the
+// base cases it saves beyond 2 048-point seed nodes (N = 65 536, eps = 1e-2:
+// 11.3 s at 6 levels, 12.7 s at 7, 21.2 s at 8).
+constexpr int kForceSeedMax = 6;
+
+// The partner table holds half of the c columns at a time (8 KB per warp), so
+// that five 4-warp CTAs (96 registers a thread) fit an SM: 20 warps.
+constexpr int kForceHalf = kTile / 2;
 struct ForceWarpSmem {
     float4 ph[3][kTile], pl[3][kTile];  // the three leaves (hi/lo)
-    float4 tab[kTile][kTile];           // partner pair (b, c): (e_bc, rho_bc)
+    float4 tab[kTile][kForceHalf];      // partner pair (b, c): (e_bc, rho_bc), c in this half
 };
 
 __device__ __forceinline__ float3 grad_from_terms(const PairFY& ab, const PairFY& ac, float4 bc) {
@@ -1542,7 +1551,7 @@ __device__ __forceinline__ float3 grad_from_terms(const PairFY& ab, const PairFY
     return g;
 }
 
-__global__ void __launch_bounds__(kForceWarps * 32)
+__global__ void __launch_bounds__(kForceWarps * 32, 5)
 base_forces_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl, int64_t N,
                    const int4* __restrict__ items, int64_t n_items, double* __restrict__ acc3) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1568,45 +1577,48 @@ base_forces_kernel(const float4* __restrict__ xh, const float4* __restrict__ xl,
         const int o1 = s == 0 ? 1 : 0, o2 = s == 2 ? 1 : 2;
         const bool same = L[o1] == L[o2];
         const bool ex1 = L[o1] == L[s], ex2 = L[o2] == L[s];
-        __syncwarp();  // the previous pass is done with the table
-        for (int e = lane; e < kTile * kTile; e += 32) {
-            const int bi = e >> 5, ci = e & 31;
-            const bool v = bi < n[o1] && ci < n[o2] && (!same || bi < ci);
-            float4 ent = z4;
-            if (v) {
-                const PairFY bc = pair_sample_y(sm.ph[o1][bi], sm.pl[o1][bi], sm.ph[o2][ci],
-                                                sm.pl[o2][ci]);
-                ent = make_float4(bc.ex, bc.ey, bc.ez, bc.rho);
-            }
-            sm.tab[bi][ci] = ent;
-        }
-        __syncwarp();
         const float4 ah = sm.ph[s][lane], al = sm.pl[s][lane];
         const bool act = lane < n[s];
         double gx = 0.0, gy = 0.0, gz = 0.0;
-        for (int cb = 0; cb < n[o2]; cb += kForceCols) {
-            PairFY ac[kForceCols];
-#pragma unroll
-            for (int q = 0; q < kForceCols; ++q) {
-                const int ci = cb + q;
-                const bool v = act && ci < n[o2] && !(ex2 && ci == lane);
-                ac[q] = pair_sample_y(ah, al, sm.ph[o2][ci & 31], sm.pl[o2][ci & 31]);
-                if (!v) ac[q] = PairFY{0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int h0 = 0; h0 < n[o2]; h0 += kForceHalf) {
+            __syncwarp();  // the previous pass is done with the table
+            for (int e = lane; e < kTile * kForceHalf; e += 32) {
+                const int bi = e / kForceHalf, cr = e % kForceHalf, ci = h0 + cr;
+                const bool v = bi < n[o1] && ci < n[o2] && (!same || bi < ci);
+                float4 ent = z4;
+                if (v) {
+                    const PairFY bc = pair_sample_y(sm.ph[o1][bi], sm.pl[o1][bi], sm.ph[o2][ci],
+                                                    sm.pl[o2][ci]);
+                    ent = make_float4(bc.ex, bc.ey, bc.ez, bc.rho);
+                }
+                sm.tab[bi][cr] = ent;
             }
-            for (int bi = 0; bi < n[o1]; ++bi) {
-                PairFY ab = pair_sample_y(ah, al, sm.ph[o1][bi], sm.pl[o1][bi]);
-                if (!act || (ex1 && bi == lane)) ab = PairFY{0.f, 0.f, 0.f, 0.f, 0.f};
-                float rx = 0.f, ry = 0.f, rz = 0.f;
+            __syncwarp();
+            const int h1 = h0 + kForceHalf < n[o2] ? h0 + kForceHalf : n[o2];
+            for (int cb = h0; cb < h1; cb += kForceCols) {
+                PairFY ac[kForceCols];
 #pragma unroll
                 for (int q = 0; q < kForceCols; ++q) {
-                    const float3 g = grad_from_terms(ab, ac[q], sm.tab[bi][(cb + q) & 31]);
-                    rx += g.x;
-                    ry += g.y;
-                    rz += g.z;
+                    const int ci = cb + q;
+                    const bool v = act && ci < n[o2] && !(ex2 && ci == lane);
+                    ac[q] = pair_sample_y(ah, al, sm.ph[o2][ci & 31], sm.pl[o2][ci & 31]);
+                    if (!v) ac[q] = PairFY{0.f, 0.f, 0.f, 0.f, 0.f};
                 }
-                gx += (double)rx;
-                gy += (double)ry;
-                gz += (double)rz;
+                for (int bi = 0; bi < n[o1]; ++bi) {
+                    PairFY ab = pair_sample_y(ah, al, sm.ph[o1][bi], sm.pl[o1][bi]);
+                    if (!act || (ex1 && bi == lane)) ab = PairFY{0.f, 0.f, 0.f, 0.f, 0.f};
+                    float rx = 0.f, ry = 0.f, rz = 0.f;
+#pragma unroll
+                    for (int q = 0; q < kForceCols; ++q) {
+                        const float3 g = grad_from_terms(ab, ac[q], sm.tab[bi][cb - h0 + q]);
+                        rx += g.x;
+                        ry += g.y;
+                        rz += g.z;
+                    }
+                    gx += (double)rx;
+                    gy += (double)ry;
+                    gz += (double)rz;
+                }
             }
         }
         if (act) {
@@ -2062,8 +2074,8 @@ static mbm_status tree_solve(mbm_ctx* ctx, const double* X, int64_t N, double ep
         MBM_CUDA_TRY(cudaMemsetAsync(pt_acc3, 0, (size_t)N * 24, s));
         MBM_CUDA_TRY(cudaMemsetAsync(node_acc3, 0, (size_t)n_nodes * 24, s));
         // A^l: exact sum of |grad_x phi|_2 over each particle's seed node
-        // (the tree's seed level), min per node bottom-up.
-        const int sd = std::max(0, tree->depth - tree->seed_levels);
+        // (the tree's seed level, at most kForceSeedMax), min per node bottom-up.
+        const int sd = std::max(0, tree->depth - std::min(tree->seed_levels, kForceSeedMax));
         const int64_t max_seed = (N + ((int64_t)1 << sd) - 1) >> sd;
         const int cpn = (int)((max_seed + 31) / 32);
         seed_scale_kernel<<<grid_of(((int64_t)1 << sd) * cpn * 32, 128), 128, 0, s>>>(
